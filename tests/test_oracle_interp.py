@@ -1,0 +1,186 @@
+"""Pins for the oracle's interpolation, footprint and adjoint (Sec. 3.1 step 3) — CPU only."""
+import numpy as np
+import pytest
+import scipy.ndimage
+
+import synth
+from oracle import interp as I
+from oracle import reproject as R
+
+
+def _golden_keys():
+    rows = {}
+    path = __file__.replace("test_oracle_interp.py", "golden/keys_weights.txt")
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            t, *w = line.split()
+            rows[float(t)] = [float(eval(x)) for x in w]
+    return rows
+
+
+def test_keys_weights_golden():
+    """Textbook Keys (a = -0.5) weights at t = 0, 0.25, 0.5 (tests/golden/keys_weights.txt)."""
+    for t, w in _golden_keys().items():
+        i0, wx = I.taps_1d(np.array([10.0 + t]), I.BICUBIC)
+        assert i0[0] == 9
+        np.testing.assert_allclose(wx[:, 0], w, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("a", [-0.5, -0.75])
+def test_keys_partition_of_unity(a):
+    t = np.linspace(0, 1, 101)[:-1]
+    _, wx = I.taps_1d(5.0 + t, I.BICUBIC, a)
+    np.testing.assert_allclose(wx.sum(axis=0), 1.0, atol=1e-15)
+
+
+def test_nearest_integer_shift_bit_exact():
+    rng = synth.rng_for(30)
+    img = rng.standard_normal((40, 50)).astype(np.float32)
+    Y, X = np.mgrid[0:40, 0:50].astype(np.float64)
+    val, fp = I.interpolate(img, X + 3.0, Y - 2.0, I.NEAREST)
+    exp = np.zeros((40, 50))
+    exp[2:, :47] = img[:38, 3:]
+    assert np.array_equal(val, exp)
+    assert set(np.unique(fp)) <= {0.0, 1.0}
+    assert np.array_equal(fp != 0, exp != 0)
+
+
+@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC])
+def test_identity_bit_exact(order):
+    rng = synth.rng_for(31)
+    img = rng.standard_normal((33, 47)).astype(np.float32)
+    Y, X = np.mgrid[0:33, 0:47].astype(np.float64)
+    eps = 1e-11 * rng.standard_normal(X.shape)  # transform round-off below the snap radius
+    val, fp = I.interpolate(img, X + eps, Y - eps, order)
+    assert np.array_equal(val.astype(np.float32), img)
+    assert np.all(fp == 1.0)
+
+
+def test_bilinear_reproduces_linear_ramp():
+    Y, X = np.mgrid[0:64, 0:80].astype(np.float64)
+    img = 0.37 * X - 1.3 * Y + 12.0
+    rng = synth.rng_for(32)
+    x = rng.uniform(0, 79, 5000)
+    y = rng.uniform(0, 63, 5000)
+    val, fp = I.interpolate(img, x, y, I.BILINEAR)
+    np.testing.assert_allclose(val, 0.37 * x - 1.3 * y + 12.0, rtol=0,
+                               atol=1e-6 * np.abs(img).max())
+    np.testing.assert_allclose(fp, 1.0, atol=1e-15)
+
+
+def test_bicubic_reproduces_quadratic():
+    Y, X = np.mgrid[0:64, 0:80].astype(np.float64)
+    f = lambda x, y: 0.01 * x * x - 0.02 * x * y + 0.005 * y * y + 0.3 * x - 0.1 * y + 2.0
+    img = f(X, Y)
+    rng = synth.rng_for(33)
+    x = rng.uniform(1, 77, 5000)
+    y = rng.uniform(1, 61, 5000)
+    val, _ = I.interpolate(img, x, y, I.BICUBIC)
+    np.testing.assert_allclose(val, f(x, y), rtol=0, atol=1e-6 * np.abs(img).max())
+
+
+@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC])
+def test_constant_image_and_footprint(order):
+    img = np.full((20, 30), 7.25)
+    rng = synth.rng_for(34)
+    x = rng.uniform(-2, 31, 20000)
+    y = rng.uniform(-2, 21, 20000)
+    val, fp = I.interpolate(img, x, y, order)
+    cov = (x >= -0.5) & (x <= 29.5) & (y >= -0.5) & (y <= 19.5) & (fp > 0)
+    assert np.all(np.abs(val[cov] - 7.25) <= 8 * np.spacing(7.25))
+    assert np.all(val[~cov] == 0) and np.all(fp[~cov] == 0)
+    inner = (x >= 2) & (x <= 27) & (y >= 2) & (y <= 17)
+    np.testing.assert_allclose(fp[inner], 1.0, atol=1e-15)
+
+
+def test_footprint_at_edges_is_in_bounds_weight_sum():
+    img = np.ones((10, 10))
+    # x = -0.5: bilinear taps -1 (out), 0 (in, w = 0.5); bicubic taps -2..1 with
+    # weights (-1/16, 9/16, 9/16, -1/16), in-bounds 0, 1 -> 0.5.
+    for order, exp in ((I.BILINEAR, 0.5), (I.BICUBIC, 0.5), (I.NEAREST, 1.0)):
+        _, fp = I.interpolate(img, np.array([-0.5]), np.array([5.0]), order)
+        assert abs(fp[0] - exp) < 1e-15
+        _, fp = I.interpolate(img, np.array([-0.5]), np.array([-0.5]), order)
+        assert abs(fp[0] - exp * exp) < 1e-15
+    _, fp = I.interpolate(img, np.array([-0.51]), np.array([5.0]), I.BILINEAR)
+    assert fp[0] == 0.0
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_matches_scipy_map_coordinates(order):
+    """Unnormalised sums equal scipy's spline interpolation of order 0/1 with zero padding."""
+    rng = synth.rng_for(35)
+    img = rng.standard_normal((30, 40))
+    x = rng.uniform(-0.5, 39.5, 4000)
+    y = rng.uniform(-0.5, 29.5, 4000)
+    if order == 0:  # keep away from rounding ties, where the two conventions differ
+        x = np.floor(x) + np.clip(x - np.floor(x), 0.01, 0.49)
+    val, fp = I.interpolate(img, x, y, order)
+    ref = scipy.ndimage.map_coordinates(img, [y, x], order=order, mode="constant", cval=0.0)
+    # scipy's constant mode returns cval for any position outside [0, n-1], so compare there
+    inner = (x >= 0) & (x <= 39) & (y >= 0) & (y <= 29)
+    assert inner.sum() > 3000
+    np.testing.assert_allclose(val[inner], ref[inner], rtol=0, atol=1e-12 if order else 0)
+    np.testing.assert_allclose(fp[inner], 1.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC])
+def test_adjoint_dot_product_and_dense(order):
+    """<W s, g> = <s, W^T g> to 1e-12, and W built column by column from unit images equals the
+    transpose built by the adjoint from unit gradients (brute force, 16x16)."""
+    rng = synth.rng_for(36)
+    H = Wd = 16
+    x = rng.uniform(-1, 16, 200)
+    y = rng.uniform(-1, 16, 200)
+    s = rng.standard_normal((H, Wd))
+    g = rng.standard_normal(200)
+    val, _ = I.interpolate(s, x, y, order)
+    adj = I.interpolate_adjoint((H, Wd), x, y, order, g)
+    assert abs(np.dot(val, g) - np.sum(s * adj)) < 1e-12 * max(1.0, abs(np.dot(val, g)))
+    Wm = np.zeros((200, H * Wd))
+    for j in range(H * Wd):
+        e = np.zeros(H * Wd)
+        e[j] = 1.0
+        Wm[:, j] = I.interpolate(e.reshape(H, Wd), x, y, order)[0]
+    Wt = np.zeros((H * Wd, 200))
+    for p in range(200):
+        e = np.zeros(200)
+        e[p] = 1.0
+        Wt[:, p] = I.interpolate_adjoint((H, Wd), x, y, order, e).ravel()
+    np.testing.assert_allclose(Wm.T, Wt, rtol=0, atol=1e-14)
+
+
+def test_reprojection_identity_wcs_bit_exact():
+    c = synth.config0()
+    src = c["src"][0]
+    img = c["images"][0]
+    for order in ("nearest", "bilinear", "bicubic"):
+        val, fp, _, _ = R.reproject(src, src, img, order)
+        assert np.array_equal(val.astype(np.float32), img)
+        assert np.all(fp == 1.0)
+
+
+def test_reprojection_integer_crpix_shift_nearest_bit_exact():
+    c = synth.config0()
+    src = c["src"][0]
+    tgt = synth.copy_wcs(src)
+    tgt["crpix"] = (src["crpix"][0] + 5.0, src["crpix"][1] - 3.0)
+    img = c["images"][0]
+    val, fp, _, _ = R.reproject(src, tgt, img, "nearest")
+    exp = np.zeros_like(val)
+    exp[:509, 5:] = img[3:, :507]
+    assert np.array_equal(val, exp)
+    assert np.array_equal(fp, (exp != 0).astype(float)) or set(np.unique(fp)) <= {0.0, 1.0}
+
+
+def test_target_bbox_contains_covered_pixels():
+    c = synth.config0()
+    src, tgt = c["src"][0], synth.copy_wcs(c["tgt"])
+    tgt["naxis"] = (700, 640)
+    tgt["crpix"] = (tgt["crpix"][0] + 60, tgt["crpix"][1] + 40)
+    x0, y0, w, h = R.target_bbox(src, tgt)
+    _, fp, _, _ = R.reproject(src, tgt, c["images"][0], "bilinear")
+    ys, xs = np.nonzero(fp)
+    assert xs.min() >= x0 and xs.max() < x0 + w and ys.min() >= y0 and ys.max() < y0 + h
+    assert w <= 512 + 20 and h <= 512 + 20
