@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Benchmark: output Mpix/s of TAN-SIP reprojection on GB300 (one JSON line on rank 0).
+
+Workload (the bench step): one 4096x4096 float32 exposure, TAN-SIP order 3 with AP/BP order 4
+(fitted by the library), reprojected with bicubic interpolation onto a 4096x4096 TAN target
+rotated 1.2 deg, offset (41.3, -17.9) px, 1% larger pixels; split precision (FP64 sky rotation
+at per-tile anchors, FP32 per pixel); value and footprint written. One step = one fused launch
+over the whole frame. Inputs are synthetic (seeded sky noise + 2000 Gaussian stars).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the launching
+stream, with a 512 MB write between steps to flush the 129 MB L2 (the flush is outside the
+events); barrier + synchronize around the timed loop; max over ranks. The reference arm
+(--impl reference) times the FP64 CPU oracle on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "output Mpix/s (bicubic, TAN-SIP) split-precision vs all-FP64 at 1e-3 px; % roofline"
+WORKLOAD = "4096x4096 TAN-SIP3 (AP/BP 4) -> 4096x4096 TAN, rot 1.2 deg, +1% scale, bicubic"
+BYTES_PER_PIX = 12  # 4 B source read + 4 B value + 4 B footprint written
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) for the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[2 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def workload():
+    c = synth.config1()
+    return c["src"][0], c["tgt"], c["images"][0]
+
+
+# ------------------------------------------------------------------------------ reference arm
+def oracle_sample_rate(src, tgt, img, npix, seed=7):
+    """Run the FP64 CPU oracle on npix random target pixels; returns seconds."""
+    from oracle import reproject as OR
+    rng = synth.rng_for(seed)
+    X = rng.integers(0, tgt["naxis"][0], npix).astype(np.float64)
+    Y = rng.integers(0, tgt["naxis"][1], npix).astype(np.float64)
+    t0 = time.perf_counter()
+    OR.reproject_pixels(src, tgt, img, X, Y, "bicubic", inverse="poly")
+    return time.perf_counter() - t0
+
+
+def oracle_wcs(src):
+    from oracle import wcs as OW
+    w, _ = OW.with_inverse_sip(src, 4)
+    return w
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    src, tgt, img = workload()
+    src = oracle_wcs(src)
+    npix = 40000
+    for _ in range(args.warmup):
+        oracle_sample_rate(src, tgt, img, npix // 4)
+    secs = [oracle_sample_rate(src, tgt, img, npix, seed=100 + k) for k in range(args.steps)]
+    t = float(np.mean(secs))
+    mpix = npix / t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_pixels_per_step": npix},
+        "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d random target pixels of the 4096^2 frame per step" % npix},
+        "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2505_03932_gb300 as dfr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    src, tgt, img = workload()
+    src, fit_max, fit_rms = dfr.fit_inverse_sip(src, 4)
+    H, W = tgt["naxis"][1], tgt["naxis"][0]
+    npix = H * W
+    img_d = torch.from_numpy(img).to(dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    fpo = torch.empty_like(out)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(precision="split"):
+        dfr.reproject(img_d, src, tgt, bbox=(0, 0, W, H), order="bicubic", precision=precision,
+                      out=out, fp_out=fpo)
+
+    def timed(k, precision):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            step(precision)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    dfr.device_status()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    times = timed(args.steps, "split")
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    dfr.device_status()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # the plain all-FP64 GPU path on the same workload (its own, shorter timing)
+    for _ in range(2):
+        step("fp64")
+    torch.cuda.synchronize()
+    ms64 = float(np.mean(timed(max(3, min(args.steps, 5)), "fp64")))
+
+    # split vs FP64 coordinate difference over the frame (both GPU paths, FP64 emitted coords)
+    _, _, c32 = dfr.reproject(img_d, src, tgt, bbox=(0, 0, W, H), order="bicubic",
+                              precision="split", coords=True)
+    _, _, c64 = dfr.reproject(img_d, src, tgt, bbox=(0, 0, W, H), order="bicubic",
+                              precision="fp64", coords=True)
+    d = torch.hypot(c32[..., 0] - c64[..., 0], c32[..., 1] - c64[..., 1])
+    d = d[torch.isfinite(d)]
+    dmax, drms = float(d.max()), float(torch.sqrt(torch.mean(d * d)))
+    del c32, c64, d
+
+    # end to end through the public API with pinned host buffers: H2D source, D2H result
+    host_img = torch.from_numpy(img).pin_memory()
+    host_out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    host_fp = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    for k in range(e2e_steps + 2):
+        if k == 2:
+            torch.cuda.synchronize()
+            te = time.perf_counter()
+        img_d.copy_(host_img, non_blocking=True)
+        step()
+        host_out.copy_(out, non_blocking=True)
+        host_fp.copy_(fpo, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / e2e_steps
+
+    peak, peak_src = _peaks()
+    achieved = BYTES_PER_PIX * npix / (ms * 1e-3) / 1e9
+    value = npix * world / (ms * 1e-3) / 1e6
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("split_bicubic_4096_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        o_src = oracle_wcs(workload()[0])
+        npx = 100000
+        secs = oracle_sample_rate(o_src, tgt, img, npx)
+        cpu = {"value": npx / secs / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": "%d random target pixels of the 4096^2 frame (%.1f s)" % (npx, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "split", "output_mpix": npix / 1e6,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "bytes_per_pixel": BYTES_PER_PIX},
+            "fp64_path": {"ms_per_step": ms64, "value": npix / (ms64 * 1e-3) / 1e6,
+                          "unit": "Mpix/s", "split_speedup": ms64 / ms},
+            "split_vs_fp64_px": {"max": dmax, "rms": drms},
+            "inverse_sip_fit_px": {"max": fit_max, "rms": fit_rms},
+            "e2e": {"value": npix * world / e2e_s / 1e6, "unit": "Mpix/s",
+                    "h2d_bytes_per_step": int(img.nbytes),
+                    "d2h_bytes_per_step": int(2 * npix * 4)},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "timed_wall_s": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/* dfr — GB300-native TAN-SIP reprojection: public C ABI.
+ *
+ * The library reprojects a source image onto a target FITS-WCS pixel grid, per target pixel:
+ *   target pixel -> (shift, SIP A/B, CD, gnomonic deprojection, native->celestial) -> (ra, dec)
+ *   -> (celestial->native, gnomonic projection, CD^-1, inverse SIP AP/BP, shift) -> source
+ *   pixel -> nearest / bilinear / bicubic interpolation normalised by the footprint.
+ * This is dfreproject (arXiv 2505.03932) Sec. 3.1 steps 1-3, with the formulas of
+ * Sec. 3.2.1 and Sec. 3.2.2, following the FITS WCS papers (Greisen & Calabretta 2002,
+ * Calabretta & Greisen 2002) and the SIP convention (Shupe et al. 2005) the paper cites.
+ *
+ * Conventions shared by every call
+ *   - Images are row-major float32, y (NAXIS2) rows of x (NAXIS1) pixels; `pitch` is the row
+ *     stride in ELEMENTS. Pixel centres sit at integer 0-based coordinates (Sec. 3.2 shifts by
+ *     one pixel from FITS' 1-based CRPIX).
+ *   - A target bounding box (x0, y0, w, h) selects target pixels x0 .. x0+w-1, y0 .. y0+h-1;
+ *     output element (i, j) holds target pixel (x0 + i, y0 + j).
+ *   - Interpolation reads taps outside the source as zero and divides by the footprint, the
+ *     in-bounds sum of the interpolation weights (Sec. 3.1, "identity tensor"). A target pixel
+ *     whose source position lies outside [-0.5, W-0.5] x [-0.5, H-0.5], or whose sky position
+ *     is on the far hemisphere of the source projection, gets value 0 and footprint 0.
+ *   - SIP polynomials use the monomials u^p v^q with 1 <= p+q <= ORDER and are ADDED:
+ *     u <- u + A(u, v), v <- v + B(u, v) (Shupe et al. 2005; the paper prints a minus sign,
+ *     which does not match the convention it cites).
+ *   - Device pointers are caller-owned CUDA device memory; `stream` is a cudaStream_t (NULL =
+ *     legacy default stream). Calls that launch work are asynchronous on that stream.
+ *   - Every call returns DFR_OK (0) or a negative DFR_ERR_* code; dfr_last_error() gives a
+ *     thread-local message for the last failure on the calling thread. Argument errors are
+ *     reported before anything is launched.
+ */
+#ifndef DFR_H_
+#define DFR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFR_ABI_VERSION 1
+
+/* status codes */
+#define DFR_OK                   0
+#define DFR_ERR_INVALID_ARG     -1  /* null/ill-sized argument, bad order or flag          */
+#define DFR_ERR_HEADER_PARSE    -2  /* malformed card or missing required keyword          */
+#define DFR_ERR_UNSUPPORTED_WCS -3  /* CTYPE not RA---TAN/DEC--TAN[-SIP], LONPOLE != 180   */
+#define DFR_ERR_SINGULAR_CD     -4  /* det(CD) == 0 or non-finite                          */
+#define DFR_ERR_NO_INVERSE_SIP  -5  /* source has A/B but no AP/BP and no exact inverse    */
+#define DFR_ERR_CUDA            -6  /* a CUDA runtime call failed                          */
+#define DFR_ERR_TIMEOUT         -7  /* a bounded device-side wait gave up                  */
+#define DFR_ERR_DEVICE          -8  /* a kernel reported a failed internal check           */
+
+/* interpolation orders (Sec. 4.2 names three schemes) */
+#define DFR_NEAREST  0
+#define DFR_BILINEAR 1
+#define DFR_BICUBIC  2   /* Keys cubic convolution, a = -0.5 */
+
+/* flags */
+#define DFR_FP64           0u  /* all-FP64 per pixel: the printed formulas, with libm trig   */
+#define DFR_SPLIT          1u  /* FP64 sky rotation at per-tile anchors, FP32 per pixel      */
+#define DFR_EXACT_INVERSE  2u  /* source inverse = Newton solve of A/B (AP/BP as start)      */
+#define DFR_NO_TMA         4u  /* gather straight from global memory instead of TMA tiles    */
+
+#define DFR_MAX_SIP 9
+
+/* WCS record. Plain data in host memory, owned by the caller. */
+typedef struct dfr_wcs {
+  int32_t naxis[2];       /* NAXIS1 (width, x), NAXIS2 (height, y)                          */
+  double  crpix[2];       /* FITS 1-based reference pixel                                   */
+  double  crval[2];       /* reference point (ra0, dec0), degrees                           */
+  double  cd[2][2];       /* CDi_j (or PCi_j * CDELTi), degrees per pixel                   */
+  int32_t a_order, b_order, ap_order, bp_order;        /* 0 = absent, at most DFR_MAX_SIP   */
+  double  a[10][10], b[10][10], ap[10][10], bp[10][10]; /* [p][q]: coefficient of u^p v^q   */
+} dfr_wcs;
+
+/* One exposure of a batch. Device pointers are caller-owned. */
+typedef struct dfr_frame {
+  dfr_wcs      wcs;        /* source WCS                                                    */
+  const float* img;        /* source image, wcs.naxis[1] rows of wcs.naxis[0] floats        */
+  int64_t      pitch;      /* source row stride, elements (>= naxis[0])                     */
+  float*       out;        /* reprojected values, h rows of w floats, row stride out_pitch  */
+  float*       footprint;  /* footprint (same layout), may be NULL                          */
+  int64_t      out_pitch;  /* output row stride, elements (>= w)                            */
+  int32_t      x0, y0, w, h; /* target bounding box; use dfr_target_bbox to size it         */
+} dfr_frame;
+
+/* Thread-local text of the last error on this thread ("" if none). Never NULL. */
+const char* dfr_last_error(void);
+
+/* Library ABI version (DFR_ABI_VERSION). */
+int dfr_abi_version(void);
+
+/* Parse a FITS header into a WCS record (Sec. 2: header reading is a cheap host step;
+ * Sec. 3.1 lists the keywords used). `cards` holds 80-character cards, either packed or
+ * newline-separated; `nbytes` is its length. Keywords: NAXISn, CTYPEn (RA---TAN / DEC--TAN,
+ * optional -SIP), CRPIXn, CRVALn, CDi_j or PCi_j with CDELTi (CD wins; CD = CDELT x PC,
+ * Sec. 3.1), optional LONPOLE (must be 180), A_ORDER/A_p_q, B_*, AP_*, BP_*. Missing
+ * keywords -> DFR_ERR_HEADER_PARSE; other projections -> DFR_ERR_UNSUPPORTED_WCS; singular
+ * CD -> DFR_ERR_SINGULAR_CD. `out` is fully written on success, untouched on failure. */
+int dfr_wcs_from_header(const char* cards, size_t nbytes, dfr_wcs* out);
+
+/* Fit inverse SIP polynomials AP/BP of the given order (1..9) to the forward A/B of `wcs`
+ * by least squares (Householder QR) on a grid over the frame plus a 5% margin, and store
+ * them in `wcs` (host memory, in place). Sec. 3.1 names SIP_INV_A/B as header content;
+ * this builds them when a header has only A/B. max_resid_px / rms_resid_px (nullable)
+ * receive the round-trip residual over a 512x512 grid of the frame. */
+int dfr_wcs_fit_inverse_sip(dfr_wcs* wcs, int32_t order, double* max_resid_px,
+                            double* rms_resid_px);
+
+/* Target-pixel bounding box of a source frame: the source boundary, sampled densely, mapped
+ * into the target grid (FP64, host), widened by 2 px and clipped to the target. Writes
+ * bbox = {x0, y0, w, h}; w = h = 0 when the frame misses the target. Host only. */
+int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]);
+
+/* Reproject one source image onto a bounding box of the target grid (Sec. 3.1 steps 1-3,
+ * Sec. 3.2). src_img: device, src->naxis[1] rows, row stride src_pitch. out: device,
+ * out_h rows of out_w values, row stride out_pitch. footprint: device, same layout, nullable.
+ * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC. flags: DFR_FP64 or DFR_SPLIT, optionally
+ * | DFR_EXACT_INVERSE | DFR_NO_TMA. coords_out (nullable, device): 2*out_w*out_h doubles,
+ * the source position (x then y per pixel, row-major) exactly as the kernel used it, NaN where
+ * the projection is undefined. Asynchronous on `stream`; out/footprint are written in full. */
+int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
+                  const float* src_img, int64_t src_pitch,
+                  float* out, float* footprint, int64_t out_pitch,
+                  int32_t x0, int32_t y0, int32_t out_w, int32_t out_h,
+                  int32_t order, uint32_t flags, double* coords_out, void* stream);
+
+/* Reproject n exposures onto one target grid in a single persistent launch (the paper's
+ * pipeline stacks >1000 exposures, Sec. 2). Every frame's pixels are computed with exactly
+ * the arithmetic of dfr_reproject for the same bounding box and flags, so results are equal
+ * bit for bit. Frames with w or h == 0 are skipped. The launch sequence for a given frame
+ * count, order and flags is captured once into a CUDA graph and replayed; tile shapes come
+ * from a built-in autotuner (first call per shape class, unless DFR_AUTOTUNE=0). The frame
+ * table is uploaded from library-owned pinned memory into library-owned device memory. */
+int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
+                        int32_t order, uint32_t flags, void* stream);
+
+/* Adjoint of dfr_reproject with respect to the source pixels and the source WCS.
+ * Given grad_out = dL/d(out) (device, out_h rows, stride go_pitch) for the same arguments as a
+ * forward call, accumulates grad_src += dL/d(src_img) (device, src->naxis[1] rows, stride
+ * gs_pitch; nullable) by scattering grad * w / footprint through the interpolation weights,
+ * and writes grad_params (device, nullable) = dL/d(theta) for the source parameters
+ *   [CRVAL1, CRVAL2 (per degree), CD1_1, CD1_2, CD2_1, CD2_2,
+ *    A_pq for 1 <= p+q <= A_ORDER (by p+q, then p descending), B_pq likewise],
+ * i.e. 6 + n_terms(A) + n_terms(B) doubles. The paper has no gradient; this extension lets
+ * alignment parameters be fitted by gradient descent. Source positions use the same
+ * arithmetic as the forward call with the same flags. Asynchronous on `stream`. */
+int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
+                           const float* src_img, int64_t src_pitch,
+                           const float* grad_out, int64_t go_pitch,
+                           int32_t x0, int32_t y0, int32_t out_w, int32_t out_h,
+                           int32_t order, uint32_t flags,
+                           float* grad_src, int64_t gs_pitch,
+                           double* grad_params, void* stream);
+
+/* Number of doubles dfr_reproject_backward writes to grad_params for this source WCS. */
+int dfr_num_params(const dfr_wcs* src);
+
+/* Read and clear the device status word that kernels set when a bounded wait gives up or an
+ * internal check fails. Synchronises `stream`. Returns DFR_OK, DFR_ERR_TIMEOUT or
+ * DFR_ERR_DEVICE. */
+int dfr_device_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFR_H_ */

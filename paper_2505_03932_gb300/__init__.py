@@ -1,0 +1,382 @@
+"""GB300-native TAN-SIP reprojection (dfreproject, arXiv 2505.03932) — Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/dfr.h`` (libdfr.so, built in place by
+``paper_2505_03932_gb300.build``). Every step of the reprojection runs in the library's CUDA
+kernels; PyTorch only supplies device memory, streams and autograd. There is no CPU fallback:
+if libdfr.so is missing or no CUDA device is present, the calls raise.
+
+WCS records are plain dicts with the fields of ``dfr_wcs``: naxis (W, H), crpix, crval (deg),
+cd (2x2, deg/px), a_order/b_order/ap_order/bp_order and a/b/ap/bp (10x10 arrays,
+[p][q] = coefficient of u^p v^q).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
+    "reproject", "reproject_batch", "reproject_backward", "calculate_reprojection",
+    "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "FP64", "SPLIT",
+    "EXACT_INVERSE", "NO_TMA",
+]
+
+NEAREST, BILINEAR, BICUBIC = 0, 1, 2
+FP64, SPLIT, EXACT_INVERSE, NO_TMA = 0, 1, 2, 4
+ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC}
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libdfr.so")
+
+
+class DfrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dfr error %d: %s" % (code, msg))
+        self.code = code
+
+
+_d2 = ctypes.c_double * 2
+_i2 = ctypes.c_int32 * 2
+_m2 = (ctypes.c_double * 2) * 2
+_s10 = (ctypes.c_double * 10) * 10
+
+
+class DfrWcs(ctypes.Structure):
+    _fields_ = [("naxis", _i2), ("crpix", _d2), ("crval", _d2), ("cd", _m2),
+                ("a_order", ctypes.c_int32), ("b_order", ctypes.c_int32),
+                ("ap_order", ctypes.c_int32), ("bp_order", ctypes.c_int32),
+                ("a", _s10), ("b", _s10), ("ap", _s10), ("bp", _s10)]
+
+
+class DfrFrame(ctypes.Structure):
+    _fields_ = [("wcs", DfrWcs), ("img", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("footprint", ctypes.c_void_p),
+                ("out_pitch", ctypes.c_int64), ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
+                ("w", ctypes.c_int32), ("h", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded libdfr.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError("libdfr.so is not built: run python -m paper_2505_03932_gb300.build")
+        L = ctypes.CDLL(_LIBPATH)
+        L.dfr_last_error.restype = ctypes.c_char_p
+        L.dfr_abi_version.restype = ctypes.c_int
+        L.dfr_wcs_from_header.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(DfrWcs)]
+        L.dfr_wcs_fit_inverse_sip.argtypes = [ctypes.POINTER(DfrWcs), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.dfr_target_bbox.argtypes = [ctypes.POINTER(DfrWcs), ctypes.POINTER(DfrWcs),
+                                      ctypes.POINTER(ctypes.c_int32)]
+        L.dfr_reproject.argtypes = [
+            ctypes.POINTER(DfrWcs), ctypes.POINTER(DfrWcs), ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
+            ctypes.c_void_p]
+        L.dfr_reproject_batch.argtypes = [ctypes.POINTER(DfrFrame), ctypes.c_int32,
+                                          ctypes.POINTER(DfrWcs), ctypes.c_int32,
+                                          ctypes.c_uint32, ctypes.c_void_p]
+        L.dfr_reproject_backward.argtypes = [
+            ctypes.POINTER(DfrWcs), ctypes.POINTER(DfrWcs), ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p]
+        L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
+        L.dfr_device_status.argtypes = [ctypes.c_void_p]
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise DfrError(rc, lib().dfr_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------------------------ WCS records
+def to_c(w) -> DfrWcs:
+    if isinstance(w, DfrWcs):
+        return w
+    c = DfrWcs()
+    c.naxis[0], c.naxis[1] = int(w["naxis"][0]), int(w["naxis"][1])
+    c.crpix[0], c.crpix[1] = float(w["crpix"][0]), float(w["crpix"][1])
+    c.crval[0], c.crval[1] = float(w["crval"][0]), float(w["crval"][1])
+    for i in range(2):
+        for j in range(2):
+            c.cd[i][j] = float(w["cd"][i][j])
+    for k in ("a", "b", "ap", "bp"):
+        setattr(c, k + "_order", int(w.get(k + "_order", 0)))
+        arr = np.zeros((10, 10)) if w.get(k) is None else np.asarray(w[k], dtype=np.float64)
+        dst = getattr(c, k)
+        for p in range(10):
+            for q in range(10):
+                dst[p][q] = float(arr[p, q])
+    return c
+
+
+def from_c(c: DfrWcs) -> dict:
+    w = {"naxis": (c.naxis[0], c.naxis[1]), "crpix": (c.crpix[0], c.crpix[1]),
+         "crval": (c.crval[0], c.crval[1]),
+         "cd": [[c.cd[0][0], c.cd[0][1]], [c.cd[1][0], c.cd[1][1]]]}
+    for k in ("a", "b", "ap", "bp"):
+        w[k + "_order"] = getattr(c, k + "_order")
+        src = getattr(c, k)
+        w[k] = np.array([[src[p][q] for q in range(10)] for p in range(10)], dtype=np.float64)
+    return w
+
+
+def wcs_from_header(text) -> dict:
+    """Parse FITS header cards (str or bytes) into a WCS record (dfr_wcs_from_header)."""
+    b = text.encode() if isinstance(text, str) else bytes(text)
+    c = DfrWcs()
+    _check(lib().dfr_wcs_from_header(b, len(b), ctypes.byref(c)))
+    return from_c(c)
+
+
+def fit_inverse_sip(w, order):
+    """Copy of ``w`` with AP/BP of ``order`` fitted (dfr_wcs_fit_inverse_sip); also returns the
+    max and RMS round-trip residual in pixels."""
+    c = to_c(w)
+    mx, rms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dfr_wcs_fit_inverse_sip(ctypes.byref(c), int(order), ctypes.byref(mx),
+                                         ctypes.byref(rms)))
+    return from_c(c), mx.value, rms.value
+
+
+def target_bbox(src, tgt):
+    """(x0, y0, w, h) of the target pixels the source frame can cover (dfr_target_bbox)."""
+    bb = (ctypes.c_int32 * 4)()
+    _check(lib().dfr_target_bbox(ctypes.byref(to_c(src)), ctypes.byref(to_c(tgt)), bb))
+    return tuple(int(v) for v in bb)
+
+
+def num_params(src) -> int:
+    n = lib().dfr_num_params(ctypes.byref(to_c(src)))
+    if n < 0:
+        _check(n)
+    return n
+
+
+def device_status(stream=None):
+    """Raise if a kernel reported a timed-out wait or a failed check since the last call."""
+    _check(lib().dfr_device_status(_stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------------------ tensors
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_f32(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2:
+        raise ValueError("%s must be a 2-D float32 CUDA tensor" % name)
+    if t.stride(1) != 1:
+        raise ValueError("%s must have unit stride along x" % name)
+    return t
+
+
+def _flags(precision, exact_inverse, tma):
+    f = SPLIT if precision == "split" else FP64
+    if precision not in ("split", "fp64"):
+        raise ValueError("precision must be 'split' or 'fp64'")
+    if exact_inverse:
+        f |= EXACT_INVERSE
+    if not tma:
+        f |= NO_TMA
+    return f
+
+
+def _order(order):
+    return ORDERS[order] if isinstance(order, str) else int(order)
+
+
+def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilinear",
+              precision="split", exact_inverse=False, footprint=True, coords=False, tma=True,
+              out=None, fp_out=None, stream=None):
+    """Reproject a device image onto the target grid (dfr_reproject).
+
+    shape_out (h, w) defaults to the target NAXIS; bbox = (x0, y0, w, h) selects part of the
+    target grid. Returns (value, footprint or None[, coords (h, w, 2) float64])."""
+    torch = _torch()
+    src_img = _dev_f32(src_img, "src_img")
+    if bbox is None:
+        if shape_out is None:
+            shape_out = (int(tgt_wcs["naxis"][1]), int(tgt_wcs["naxis"][0]))
+        bbox = (0, 0, int(shape_out[1]), int(shape_out[0]))
+    x0, y0, w, h = (int(v) for v in bbox)
+    dev = src_img.device
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.float32, device=dev)
+    out = _dev_f32(out, "out")
+    fp = None
+    if footprint:
+        fp = fp_out if fp_out is not None else torch.empty((h, w), dtype=torch.float32, device=dev)
+        fp = _dev_f32(fp, "footprint")
+    cr = torch.empty((h, w, 2), dtype=torch.float64, device=dev) if coords else None
+    _check(lib().dfr_reproject(
+        ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)), ctypes.c_void_p(src_img.data_ptr()),
+        src_img.stride(0), ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(fp.data_ptr() if fp is not None else 0), out.stride(0), x0, y0, w, h,
+        _order(order), _flags(precision, exact_inverse, tma),
+        ctypes.c_void_p(cr.data_ptr() if cr is not None else 0), _stream_ptr(stream)))
+    return (out, fp, cr) if coords else (out, fp)
+
+
+def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear",
+                    precision="split", outs=None, fps=None, footprint=True, stream=None):
+    """Reproject many exposures in one persistent launch (dfr_reproject_batch).
+
+    bboxes default to dfr_target_bbox per frame. Returns (values, footprints) lists."""
+    torch = _torch()
+    n = len(images)
+    frames = (DfrFrame * max(n, 1))()
+    vals, fpl = [], []
+    for i in range(n):
+        img = _dev_f32(images[i], "images[%d]" % i)
+        bb = bboxes[i] if bboxes is not None else target_bbox(src_wcs_list[i], tgt_wcs)
+        x0, y0, w, h = (int(v) for v in bb)
+        o = outs[i] if outs is not None else torch.empty((max(h, 1), max(w, 1)),
+                                                          dtype=torch.float32, device=img.device)
+        f = None
+        if footprint:
+            f = fps[i] if fps is not None else torch.empty_like(o)
+        fr = frames[i]
+        fr.wcs = to_c(src_wcs_list[i])
+        fr.img = img.data_ptr()
+        fr.pitch = img.stride(0)
+        fr.out = o.data_ptr()
+        fr.footprint = f.data_ptr() if f is not None else 0
+        fr.out_pitch = o.stride(0)
+        fr.x0, fr.y0, fr.w, fr.h = x0, y0, w, h
+        vals.append(o)
+        fpl.append(f)
+    _check(lib().dfr_reproject_batch(frames, n, ctypes.byref(to_c(tgt_wcs)), _order(order),
+                                     _flags(precision, False, True), _stream_ptr(stream)))
+    return vals, fpl
+
+
+def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinear",
+                       precision="split", exact_inverse=False, grad_src=None, want_src=True,
+                       want_params=True, stream=None):
+    """Adjoint of reproject (dfr_reproject_backward): returns (grad_src, grad_params)."""
+    torch = _torch()
+    src_img = _dev_f32(src_img, "src_img")
+    grad_out = _dev_f32(grad_out, "grad_out")
+    x0, y0, w, h = (int(v) for v in bbox)
+    gs = None
+    if want_src:
+        gs = grad_src if grad_src is not None else torch.zeros_like(src_img)
+        gs = _dev_f32(gs, "grad_src")
+    gp = torch.zeros(num_params(src_wcs), dtype=torch.float64, device=src_img.device) \
+        if want_params else None
+    _check(lib().dfr_reproject_backward(
+        ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)),
+        ctypes.c_void_p(src_img.data_ptr()), src_img.stride(0),
+        ctypes.c_void_p(grad_out.data_ptr()), grad_out.stride(0), x0, y0, w, h, _order(order),
+        _flags(precision, exact_inverse, True),
+        ctypes.c_void_p(gs.data_ptr() if gs is not None else 0), gs.stride(0) if gs is not None else 0,
+        ctypes.c_void_p(gp.data_ptr() if gp is not None else 0), _stream_ptr(stream)))
+    return gs, gp
+
+
+def calculate_reprojection(source_img, source_wcs, target_wcs, shape_out=None, order="bilinear",
+                           precision="split"):
+    """Paper-style call (Sec. 2): host image in, host (value, footprint) out.
+
+    ``source_wcs`` / ``target_wcs`` may be WCS records or FITS header text. The image is copied
+    to the current CUDA device, reprojected there and copied back; ``shape_out`` defaults to
+    the target NAXIS (the input shape when the target header has none of its own)."""
+    torch = _torch()
+    if isinstance(source_wcs, (str, bytes)):
+        source_wcs = wcs_from_header(source_wcs)
+    if isinstance(target_wcs, (str, bytes)):
+        target_wcs = wcs_from_header(target_wcs)
+    host = torch.as_tensor(np.asarray(source_img, dtype=np.float32))
+    dev = host.to("cuda", non_blocking=True)
+    val, fp = reproject(dev, source_wcs, target_wcs, shape_out=shape_out, order=order,
+                        precision=precision)
+    return val.cpu().numpy(), fp.cpu().numpy()
+
+
+def _autograd():
+    torch = _torch()
+
+    class Reproject(torch.autograd.Function):
+        """value = reproject(src_img; src WCS parameters theta). Differentiable with respect to
+        the source image and the parameter vector theta (layout of dfr_reproject_backward)."""
+
+        @staticmethod
+        def forward(ctx, src_img, theta, src_wcs, tgt_wcs, bbox, order, precision, exact_inverse):
+            w = set_params(src_wcs, theta.detach().cpu().numpy())
+            val, _ = reproject(src_img, w, tgt_wcs, bbox=bbox, order=order, precision=precision,
+                               exact_inverse=exact_inverse, footprint=False)
+            ctx.save_for_backward(src_img)
+            ctx.cfg = (w, tgt_wcs, bbox, order, precision, exact_inverse)
+            return val
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (src_img,) = ctx.saved_tensors
+            w, tgt_wcs, bbox, order, precision, exact_inverse = ctx.cfg
+            gs, gp = reproject_backward(src_img, w, tgt_wcs, grad_out.contiguous(), bbox, order,
+                                        precision, exact_inverse,
+                                        want_src=ctx.needs_input_grad[0],
+                                        want_params=ctx.needs_input_grad[1])
+            return gs, gp, None, None, None, None, None, None
+
+    return Reproject
+
+
+def param_vector(w):
+    """Source parameter vector in the dfr_reproject_backward layout."""
+    vals = [w["crval"][0], w["crval"][1], w["cd"][0][0], w["cd"][0][1], w["cd"][1][0],
+            w["cd"][1][1]]
+    for k in ("a", "b"):
+        arr = np.asarray(w[k])
+        for n in range(1, int(w[k + "_order"]) + 1):
+            for p in range(n, -1, -1):
+                vals.append(float(arr[p, n - p]))
+    return np.array(vals, dtype=np.float64)
+
+
+def set_params(w, theta):
+    """Copy of w with the parameter vector ``theta`` written back."""
+    out = dict(w)
+    out["crval"] = (float(theta[0]), float(theta[1]))
+    out["cd"] = [[float(theta[2]), float(theta[3])], [float(theta[4]), float(theta[5])]]
+    idx = 6
+    for k in ("a", "b"):
+        arr = np.array(w[k], dtype=np.float64, copy=True)
+        for n in range(1, int(w[k + "_order"]) + 1):
+            for p in range(n, -1, -1):
+                arr[p, n - p] = theta[idx]
+                idx += 1
+        out[k] = arr
+    return out
+
+
+class _LazyReproject:
+    _cls = None
+
+    def apply(self, *args):
+        if _LazyReproject._cls is None:
+            _LazyReproject._cls = _autograd()
+        return _LazyReproject._cls.apply(*args)
+
+
+Reproject = _LazyReproject()

@@ -1,0 +1,391 @@
+// Device helpers shared by the forward and backward kernels: SIP polynomials (Horner in
+// registers), the FP64 per-pixel transform of Sec. 3.2.1 / 3.2.2, the split-precision tile
+// anchor, interpolation weights, and the TMA / mbarrier primitives.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dfr_internal.h"
+
+namespace dfr {
+
+// Device status word of this translation unit (each kernel file has its own copy).
+static __device__ int32_t g_status = 0;
+
+constexpr double kR0 = 57.295779513082320876798154814105;  // 180 / pi
+constexpr double kSnap = 1e-9;                               // FP64 integer snap radius, px
+
+// ---------------------------------------------------------------- polynomials (Horner)
+// Fixed degree N, coefficients of two polynomials (A and B) evaluated at the same (u, v).
+template <int N, typename T>
+__device__ __forceinline__ void horner_pair(const T* __restrict__ ca, const T* __restrict__ cb,
+                                            T u, T v, T& A, T& B) {
+  T pa = T(0), pb = T(0);
+#pragma unroll
+  for (int p = N; p >= 0; --p) {
+    const int off = poly_off(p, N);
+    T qa = ca[off + (N - p)], qb = cb[off + (N - p)];
+#pragma unroll
+    for (int q = N - p - 1; q >= 0; --q) {
+      qa = fma(qa, v, ca[off + q]);
+      qb = fma(qb, v, cb[off + q]);
+    }
+    if (p == N) {
+      pa = qa;
+      pb = qb;
+    } else {
+      pa = fma(pa, u, qa);
+      pb = fma(pb, u, qb);
+    }
+  }
+  A = pa;
+  B = pb;
+}
+
+// Runtime degree n (FP64 path and rarely used branches).
+template <typename T>
+__device__ __forceinline__ void horner_pair_rt(const T* ca, const T* cb, int n, T u, T v,
+                                               T& A, T& B) {
+  T pa = T(0), pb = T(0);
+  for (int p = n; p >= 0; --p) {
+    const int off = poly_off(p, n);
+    T qa = ca[off + (n - p)], qb = cb[off + (n - p)];
+    for (int q = n - p - 1; q >= 0; --q) {
+      qa = fma(qa, v, ca[off + q]);
+      qb = fma(qb, v, cb[off + q]);
+    }
+    pa = (p == n) ? qa : fma(pa, u, qa);
+    pb = (p == n) ? qb : fma(pb, u, qb);
+  }
+  A = pa;
+  B = pb;
+}
+
+// Value and first partials of one polynomial (runtime degree): P, dP/du, dP/dv.
+template <typename T>
+__device__ __forceinline__ void horner_grad_rt(const T* c, int n, T u, T v, T& P, T& Pu, T& Pv) {
+  T p_ = T(0), pu = T(0), pv = T(0);
+  for (int p = n; p >= 0; --p) {
+    const int off = poly_off(p, n);
+    T q_ = c[off + (n - p)], qv = T(0);
+    for (int q = n - p - 1; q >= 0; --q) {
+      qv = fma(qv, v, q_);
+      q_ = fma(q_, v, c[off + q]);
+    }
+    pu = fma(pu, u, p_);
+    p_ = fma(p_, u, q_);
+    pv = fma(pv, u, qv);
+  }
+  P = p_;
+  Pu = pu;
+  Pv = pv;
+}
+
+// ---------------------------------------------------------------- interpolation weights
+// Taps start at floor(x) + kLo[order]; count kTaps[order].
+template <int ORDER> struct Taps;
+template <> struct Taps<DFR_NEAREST> { static constexpr int n = 1, lo = 0; };
+template <> struct Taps<DFR_BILINEAR> { static constexpr int n = 2, lo = 0; };
+template <> struct Taps<DFR_BICUBIC> { static constexpr int n = 4, lo = -1; };
+
+// t = x - floor(x) in [0, 1). Nearest is handled by the caller (index shift when t >= 1/2).
+template <int ORDER, typename T>
+__device__ __forceinline__ void weights(T t, T* w) {
+  if (ORDER == DFR_NEAREST) {
+    w[0] = T(1);
+  } else if (ORDER == DFR_BILINEAR) {
+    w[0] = T(1) - t;
+    w[1] = t;
+  } else {
+    // Keys cubic convolution, a = -0.5, at distances 1+t, t, 1-t, 2-t
+    const T s = T(1) - t;
+    const T t2 = t * t, s2 = s * s;
+    w[0] = (T(-0.5) * t) * s2;
+    w[1] = fma(t2, fma(T(1.5), t, T(-2.5)), T(1));
+    w[2] = fma(s2, fma(T(1.5), s, T(-2.5)), T(1));
+    w[3] = (T(-0.5) * t2) * s;
+  }
+}
+
+// d(weights)/dt for the backward pass.
+template <int ORDER, typename T>
+__device__ __forceinline__ void dweights(T t, T* d) {
+  if (ORDER == DFR_NEAREST) {
+    d[0] = T(0);
+  } else if (ORDER == DFR_BILINEAR) {
+    d[0] = T(-1);
+    d[1] = T(1);
+  } else {
+    const T s = T(1) - t;
+    // w0 = -t s^2 / 2          -> -(s^2)/2 + t s
+    // w1 = 1.5 t^3 - 2.5 t^2 + 1 -> 4.5 t^2 - 5 t
+    // w2 = 1.5 s^3 - 2.5 s^2 + 1 -> -(4.5 s^2 - 5 s)
+    // w3 = -t^2 s / 2          -> -t s + t^2 / 2
+    d[0] = fma(T(-0.5) * s, s, t * s);
+    d[1] = t * fma(T(4.5), t, T(-5));
+    d[2] = -(s * fma(T(4.5), s, T(-5)));
+    d[3] = fma(T(0.5) * t, t, -(t * s));
+  }
+}
+
+// ---------------------------------------------------------------- FP64 per-pixel transform
+// Sec. 3.2.1 then Sec. 3.2.2, literally, in FP64 (the two asin steps as atan2(z, hypot(x, y)),
+// the same angle, well conditioned near the tangent point and the poles).
+__device__ __forceinline__ void world_from_target_fp64(const FwdPlan& P, double X, double Y,
+                                                       double& ra, double& dec) {
+  double u = X - P.crpix_t[0];
+  double v = Y - P.crpix_t[1];
+  if (P.tsip_deg > 0) {
+    double fa, fb;
+    horner_pair_rt<double>(P.tsip_d[0], P.tsip_d[1], P.tsip_deg, u, v, fa, fb);
+    u += fa;
+    v += fb;
+  }
+  const double up = P.cd_t[0][0] * u + P.cd_t[0][1] * v;
+  const double vp = P.cd_t[1][0] * u + P.cd_t[1][1] * v;
+  const double r = sqrt(up * up + vp * vp);
+  const double phi = atan2(-up, vp);
+  const double theta = atan2(kR0, r);
+  double st, ct, sp, cp;
+  sincos(theta, &st, &ct);
+  sincos(phi, &sp, &cp);
+  const double z = st * P.sd0_t + ct * P.cd0_t * cp;
+  const double ya = -ct * sp;
+  const double xa = st * P.cd0_t - ct * P.sd0_t * cp;
+  dec = atan2(z, sqrt(ya * ya + xa * xa));
+  ra = P.ra0_t + atan2(ya, xa);
+}
+
+// Returns false where the source projection is undefined (sin theta <= 0).
+__device__ __forceinline__ bool intermediate_from_world_fp64(const FwdPlan& P, double ra,
+                                                             double dec, double& U, double& V) {
+  const double dra = ra - P.ra0_s;
+  double sd, cdn, sdra, cdra;
+  sincos(dec, &sd, &cdn);
+  sincos(dra, &sdra, &cdra);
+  const double n1 = -cdn * sdra;
+  const double n2 = sd * P.cd0_s - cdn * P.sd0_s * cdra;
+  const double dd = sd * P.sd0_s + cdn * P.cd0_s * cdra;
+  const double phi = atan2(n1, n2);
+  const double theta = atan2(dd, sqrt(n1 * n1 + n2 * n2));
+  double st, ct, sp, cp;
+  sincos(theta, &st, &ct);
+  sincos(phi, &sp, &cp);
+  const double r = kR0 * ct / st;
+  const double up = -r * sp;
+  const double vp = r * cp;
+  U = P.cdinv_s[0][0] * up + P.cdinv_s[0][1] * vp;
+  V = P.cdinv_s[1][0] * up + P.cdinv_s[1][1] * vp;
+  return st > 0.0;
+}
+
+// Newton solve of u + A(u, v) = U, v + B(u, v) = V (FP64), started from (u, v).
+__device__ __forceinline__ void newton_fp64(const FwdPlan& P, double U, double V, double& u,
+                                            double& v) {
+  for (int it = 0; it < 30; ++it) {
+    double A, Au, Av, B, Bu, Bv;
+    horner_grad_rt<double>(P.fsip_d[0], P.fsip_deg, u, v, A, Au, Av);
+    horner_grad_rt<double>(P.fsip_d[1], P.fsip_deg, u, v, B, Bu, Bv);
+    const double fu = u + A - U, fv = v + B - V;
+    const double j00 = 1.0 + Au, j01 = Av, j10 = Bu, j11 = 1.0 + Bv;
+    const double det = j00 * j11 - j01 * j10;
+    const double du = (j11 * fu - j01 * fv) / det;
+    const double dv = (j00 * fv - j10 * fu) / det;
+    u -= du;
+    v -= dv;
+    if (fabs(du) < 1e-12 && fabs(dv) < 1e-12) break;
+  }
+}
+
+__device__ __forceinline__ bool source_from_target_fp64(const FwdPlan& P, double X, double Y,
+                                                        double& xs, double& ys) {
+  if (P.identity) {
+    xs = X;
+    ys = Y;
+    return true;
+  }
+  double ra, dec, U, V;
+  world_from_target_fp64(P, X, Y, ra, dec);
+  const bool ok = intermediate_from_world_fp64(P, ra, dec, U, V);
+  double u = U, v = V;
+  if (P.isip_deg > 0) {
+    double ga, gb;
+    horner_pair_rt<double>(P.isip_d[0], P.isip_d[1], P.isip_deg, U, V, ga, gb);
+    u = U + ga;
+    v = V + gb;
+  }
+  if ((P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0) newton_fp64(P, U, V, u, v);
+  xs = u + P.crpix_s[0];
+  ys = v + P.crpix_s[1];
+  return ok;
+}
+
+// ---------------------------------------------------------------- split-precision anchor
+// FP64 part of the split path, once per 64x16 tile: the homography at the tile's anchor
+// pixel and the FP32 coefficients of its local expansion.
+struct Anchor {
+  int32_t bx, by;        // integer part of the anchor's source position
+  int32_t ax, ay;        // anchor target pixel (absolute)
+  float f0x, f0y;        // anchor source position minus (bx, by)
+  float U0, V0;          // anchor source intermediate offsets (for SIP evaluation)
+  float a0, a1, b0, b1;  // numerators of the local homography
+  float g20, g21, h2;    // its denominator
+  float tu, tv, tA, tB;  // target SIP argument and value at the anchor (FP32)
+};
+
+__device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
+  a.ax = ax;
+  a.ay = ay;
+  if (P.identity) {
+    a.bx = ax;
+    a.by = ay;
+    a.f0x = a.f0y = 0.f;
+    a.U0 = a.V0 = 0.f;
+    a.a0 = 1.f; a.a1 = 0.f; a.b0 = 0.f; a.b1 = 1.f;
+    a.g20 = a.g21 = 0.f;
+    a.h2 = 1.f;
+    a.tu = a.tv = a.tA = a.tB = 0.f;
+    return;
+  }
+  const double u = double(ax) - P.crpix_t[0];
+  const double v = double(ay) - P.crpix_t[1];
+  double p = u, q = v;
+  a.tu = float(u);
+  a.tv = float(v);
+  a.tA = a.tB = 0.f;
+  if (P.tsip_deg > 0) {
+    double fa, fb;
+    horner_pair_rt<double>(P.tsip_d[0], P.tsip_d[1], P.tsip_deg, u, v, fa, fb);
+    p += fa;
+    q += fb;
+    float ga, gb;
+    horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, a.tu, a.tv, ga, gb);
+    a.tA = ga;
+    a.tB = gb;
+  }
+  const double h0 = P.G[0][0] * p + P.G[0][1] * q + P.G[0][2];
+  const double h1 = P.G[1][0] * p + P.G[1][1] * q + P.G[1][2];
+  const double h2 = P.G[2][0] * p + P.G[2][1] * q + P.G[2][2];
+  const double U0 = h0 / h2, V0 = h1 / h2;
+  a.a0 = float(P.G[0][0] - U0 * P.G[2][0]);
+  a.a1 = float(P.G[0][1] - U0 * P.G[2][1]);
+  a.b0 = float(P.G[1][0] - V0 * P.G[2][0]);
+  a.b1 = float(P.G[1][1] - V0 * P.G[2][1]);
+  a.g20 = float(P.G[2][0]);
+  a.g21 = float(P.G[2][1]);
+  a.h2 = float(h2);
+  a.U0 = float(U0);
+  a.V0 = float(V0);
+  const double X0 = U0 + P.crpix_s[0], Y0 = V0 + P.crpix_s[1];
+  const double fx = floor(X0), fy = floor(Y0);
+  const bool finite = isfinite(X0) && isfinite(Y0) && fabs(X0) < 1e9 && fabs(Y0) < 1e9;
+  a.bx = finite ? int32_t(fx) : 0;
+  a.by = finite ? int32_t(fy) : 0;
+  a.f0x = finite ? float(X0 - fx) : 0.f;
+  a.f0y = finite ? float(Y0 - fy) : 0.f;
+  if (!finite || !(h2 > 0.0)) a.h2 = -1.f;  // the whole tile is treated as uncovered
+}
+
+// FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor pixel.
+// Writes the source position relative to (bx, by); returns false if undefined.
+template <int IDEG>
+__device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, float dx,
+                                             float dy, float& xr, float& yr) {
+  if (P.identity) {
+    xr = dx;
+    yr = dy;
+    return true;
+  }
+  float dp = dx, dq = dy;
+  if (P.tsip_deg > 0) {
+    float fa, fb;
+    horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, a.tu + dx, a.tv + dy, fa, fb);
+    dp = dx + (fa - a.tA);
+    dq = dy + (fb - a.tB);
+  }
+  const float nu = fmaf(a.a0, dp, a.a1 * dq);
+  const float nv = fmaf(a.b0, dp, a.b1 * dq);
+  const float den = fmaf(a.g20, dp, fmaf(a.g21, dq, a.h2));
+  const float rcp = __fdividef(1.f, den);
+  float du = nu * rcp, dv = nv * rcp;
+  float eu = du, ev = dv;
+  if (IDEG > 0) {
+    float ga, gb;
+    horner_pair<IDEG, float>(P.isip_f[0], P.isip_f[1], a.U0 + du, a.V0 + dv, ga, gb);
+    eu = du + ga;
+    ev = dv + gb;
+  }
+  if ((P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0) {
+    // Newton on e = u - U0: e + A(U0 + e) = du, started from the AP/BP estimate.
+    for (int it = 0; it < P.newton_iters; ++it) {
+      float A, Au, Av, B, Bu, Bv;
+      horner_grad_rt<float>(P.fsip_f[0], P.fsip_deg, a.U0 + eu, a.V0 + ev, A, Au, Av);
+      horner_grad_rt<float>(P.fsip_f[1], P.fsip_deg, a.U0 + eu, a.V0 + ev, B, Bu, Bv);
+      const float ru = (eu - du) + A, rv = (ev - dv) + B;
+      const float j00 = 1.f + Au, j11 = 1.f + Bv;
+      const float det = fmaf(j00, j11, -Av * Bu);
+      const float inv = __fdividef(1.f, det);
+      eu -= fmaf(j11, ru, -Av * rv) * inv;
+      ev -= fmaf(j00, rv, -Bu * ru) * inv;
+    }
+  }
+  xr = a.f0x + eu;
+  yr = a.f0y + ev;
+  return den > 0.f && a.h2 > 0.f;
+}
+
+// ---------------------------------------------------------------- TMA and mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; on give-up sets the device status and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(&g_status, kStatusTimeout);
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 2-D tiled TMA load of the box at (x, y) (x a multiple of 4 floats) into shared memory.
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+}  // namespace dfr

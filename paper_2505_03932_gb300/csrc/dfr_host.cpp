@@ -1,0 +1,966 @@
+// Host side of libdfr: the C ABI, FITS header parsing, the FP64 plan builder, the inverse-SIP
+// fit, bounding boxes, TMA tensor maps, and the batched launch (CUDA graph + autotuner).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "dfr_internal.h"
+
+namespace dfr {
+namespace {
+
+// ------------------------------------------------------------------------------ errors
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(DFR_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define DFR_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kDeg = kPi / 180.0;
+constexpr double kR0 = 180.0 / kPi;
+
+// ------------------------------------------------------------------------------ FITS cards
+struct Card {
+  bool is_str = false;
+  std::string s;
+  double d = 0.0;
+};
+
+std::string trim(const std::string& s) {
+  size_t a = 0, b = s.size();
+  while (a < b && std::isspace(static_cast<unsigned char>(s[a]))) ++a;
+  while (b > a && std::isspace(static_cast<unsigned char>(s[b - 1]))) --b;
+  return s.substr(a, b - a);
+}
+
+bool parse_value(const std::string& raw, Card& c) {
+  std::string s = trim(raw);
+  if (!s.empty() && s[0] == '\'') {
+    std::string out;
+    size_t i = 1;
+    for (; i < s.size(); ++i) {
+      if (s[i] == '\'') {
+        if (i + 1 < s.size() && s[i + 1] == '\'') {
+          out.push_back('\'');
+          ++i;
+        } else {
+          break;
+        }
+      } else {
+        out.push_back(s[i]);
+      }
+    }
+    if (i >= s.size()) return false;
+    while (!out.empty() && out.back() == ' ') out.pop_back();
+    c.is_str = true;
+    c.s = out;
+    return true;
+  }
+  size_t slash = s.find('/');
+  if (slash != std::string::npos) s = trim(s.substr(0, slash));
+  if (s == "T" || s == "F") {
+    c.d = (s == "T") ? 1.0 : 0.0;
+    return true;
+  }
+  for (char& ch : s)
+    if (ch == 'D' || ch == 'd') ch = 'E';
+  if (s.empty()) return false;
+  char* end = nullptr;
+  c.d = std::strtod(s.c_str(), &end);
+  return end && *end == '\0';
+}
+
+bool sip_name(const std::string& key, const char* pfx, int& p, int& q) {
+  const size_t n = std::strlen(pfx);
+  if (key.compare(0, n, pfx) != 0) return false;
+  int a, b;
+  char tail;
+  if (std::sscanf(key.c_str() + n, "%d_%d%c", &a, &b, &tail) != 2) return false;
+  p = a;
+  q = b;
+  return true;
+}
+
+// ------------------------------------------------------------------------------ WCS checks
+bool finite_wcs(const dfr_wcs& w) {
+  for (int i = 0; i < 2; ++i) {
+    if (!std::isfinite(w.crpix[i]) || !std::isfinite(w.crval[i])) return false;
+    for (int j = 0; j < 2; ++j)
+      if (!std::isfinite(w.cd[i][j])) return false;
+  }
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q)
+      if (!std::isfinite(w.a[p][q]) || !std::isfinite(w.b[p][q]) || !std::isfinite(w.ap[p][q]) ||
+          !std::isfinite(w.bp[p][q]))
+        return false;
+  return true;
+}
+
+int check_wcs(const dfr_wcs* w, const char* name) {
+  if (!w) return fail(DFR_ERR_INVALID_ARG, "%s WCS is NULL", name);
+  if (w->naxis[0] <= 0 || w->naxis[1] <= 0)
+    return fail(DFR_ERR_INVALID_ARG, "%s NAXIS must be positive", name);
+  for (int o : {w->a_order, w->b_order, w->ap_order, w->bp_order})
+    if (o < 0 || o > DFR_MAX_SIP)
+      return fail(DFR_ERR_INVALID_ARG, "%s SIP order out of range 0..9", name);
+  if (!finite_wcs(*w)) return fail(DFR_ERR_INVALID_ARG, "%s WCS has non-finite values", name);
+  const double det = w->cd[0][0] * w->cd[1][1] - w->cd[0][1] * w->cd[1][0];
+  if (!(det != 0.0) || !std::isfinite(det)) return fail(DFR_ERR_SINGULAR_CD, "%s CD is singular", name);
+  return DFR_OK;
+}
+
+void cd_inverse(const double cd[2][2], double inv[2][2]) {
+  const double det = cd[0][0] * cd[1][1] - cd[0][1] * cd[1][0];
+  inv[0][0] = cd[1][1] / det;
+  inv[0][1] = -cd[0][1] / det;
+  inv[1][0] = -cd[1][0] / det;
+  inv[1][1] = cd[0][0] / det;
+}
+
+// Tangent-plane frame at (ra0, dec0): columns (east, north, tangent point) unit vectors.
+void tangent_frame(double ra0_deg, double dec0_deg, double F[3][3]) {
+  const double a = ra0_deg * kDeg, d = dec0_deg * kDeg;
+  const double ca = std::cos(a), sa = std::sin(a), cdd = std::cos(d), sd = std::sin(d);
+  const double ex[3] = {-sa, ca, 0.0};
+  const double ey[3] = {-sd * ca, -sd * sa, cdd};
+  const double e0[3] = {cdd * ca, cdd * sa, sd};
+  for (int i = 0; i < 3; ++i) {
+    F[i][0] = ex[i];
+    F[i][1] = ey[i];
+    F[i][2] = e0[i];
+  }
+}
+
+int sip_round_degree(int order) {
+  if (order <= 0) return 0;
+  if (order <= 4) return 4;
+  if (order <= 6) return 6;
+  return 9;
+}
+
+template <typename T>
+void pack_poly(const double c[10][10], int order, int deg, T* out) {
+  for (int k = 0; k < kMaxCoef; ++k) out[k] = T(0);
+  for (int p = 0; p <= deg; ++p)
+    for (int q = 0; q <= deg - p; ++q)
+      if (p + q >= 1 && p + q <= order) out[poly_off(p, deg) + q] = T(c[p][q]);
+}
+
+double poly_eval(const double c[10][10], int order, double u, double v) {
+  double s = 0.0;
+  for (int p = 0; p <= order; ++p) {
+    double up = std::pow(u, p);
+    for (int q = 0; q <= order - p; ++q)
+      if (p + q >= 1) s += c[p][q] * up * std::pow(v, q);
+  }
+  return s;
+}
+
+bool same_linear(const dfr_wcs& a, const dfr_wcs& b) {
+  return std::memcmp(a.crpix, b.crpix, sizeof(a.crpix)) == 0 &&
+         std::memcmp(a.crval, b.crval, sizeof(a.crval)) == 0 &&
+         std::memcmp(a.cd, b.cd, sizeof(a.cd)) == 0;
+}
+
+bool same_sip(const dfr_wcs& a, const dfr_wcs& b) {
+  return a.a_order == b.a_order && a.b_order == b.b_order &&
+         std::memcmp(a.a, b.a, sizeof(a.a)) == 0 && std::memcmp(a.b, b.b, sizeof(a.b)) == 0;
+}
+
+// ------------------------------------------------------------------------------ TMA maps
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// ------------------------------------------------------------------------------ plan
+struct HostMap {
+  // FP64 host evaluation of the split map (homography + SIP), for box sizing and bboxes
+  const FwdPlan* P;
+  bool eval(double X, double Y, double& xs, double& ys) const {
+    const double p = X - P->crpix_t[0], q = Y - P->crpix_t[1];
+    xs = ys = 0.0;
+    return map_pq(p, q, X, Y, xs, ys);
+  }
+  bool map_pq(double p, double q, double, double, double& xs, double& ys) const;
+};
+
+}  // namespace
+
+// Exposed for the batch and backward paths in this file.
+struct PlanCtx {
+  dfr_wcs src, tgt;
+};
+
+static double horner_host(const double* c, int n, double u, double v) {
+  double P = 0.0;
+  for (int p = n; p >= 0; --p) {
+    const int off = poly_off(p, n);
+    double Q = c[off + (n - p)];
+    for (int q = n - p - 1; q >= 0; --q) Q = std::fma(Q, v, c[off + q]);
+    P = (p == n) ? Q : std::fma(P, u, Q);
+  }
+  return P;
+}
+
+bool HostMap::map_pq(double p, double q, double, double, double& xs, double& ys) const {
+  const FwdPlan& F = *P;
+  if (F.tsip_deg > 0) {
+    const double u = p, v = q;
+    p = u + horner_host(F.tsip_d[0], F.tsip_deg, u, v);
+    q = v + horner_host(F.tsip_d[1], F.tsip_deg, u, v);
+  }
+  const double h0 = F.G[0][0] * p + F.G[0][1] * q + F.G[0][2];
+  const double h1 = F.G[1][0] * p + F.G[1][1] * q + F.G[1][2];
+  const double h2 = F.G[2][0] * p + F.G[2][1] * q + F.G[2][2];
+  if (!(h2 > 0.0)) return false;
+  double U = h0 / h2, V = h1 / h2;
+  double u = U, v = V;
+  if (F.isip_deg > 0) {
+    u = U + horner_host(F.isip_d[0], F.isip_deg, U, V);
+    v = V + horner_host(F.isip_d[1], F.isip_deg, U, V);
+  }
+  xs = u + F.crpix_s[0];
+  ys = v + F.crpix_s[1];
+  return std::isfinite(xs) && std::isfinite(ys);
+}
+
+namespace {
+
+// Source-box size for the TMA staging of one 64x16 tile: the largest source extent of a tile,
+// estimated from the map's Jacobian on a grid over the bounding box, with a 10% margin.
+void size_box(FwdPlan& P) {
+  HostMap M{&P};
+  const int ns = 17;
+  double jxx = 0, jxy = 0, jyx = 0, jyy = 0;
+  for (int j = 0; j < ns; ++j)
+    for (int i = 0; i < ns; ++i) {
+      const double X = P.x0 + (P.w - 1) * double(i) / (ns - 1);
+      const double Y = P.y0 + (P.h - 1) * double(j) / (ns - 1);
+      double x0, y0, x1, y1, x2, y2;
+      if (!M.eval(X, Y, x0, y0) || !M.eval(X + 1, Y, x1, y1) || !M.eval(X, Y + 1, x2, y2))
+        continue;
+      jxx = std::max(jxx, std::fabs(x1 - x0));
+      jyx = std::max(jyx, std::fabs(y1 - y0));
+      jxy = std::max(jxy, std::fabs(x2 - x0));
+      jyy = std::max(jyy, std::fabs(y2 - y0));
+    }
+  const int ext = (P.order == DFR_BICUBIC) ? 4 : 2;
+  const double sx = 1.1 * (jxx * (kTileW - 1) + jxy * (kTileH - 1)) + 1.0;
+  const double sy = 1.1 * (jyx * (kTileW - 1) + jyy * (kTileH - 1)) + 1.0;
+  int bw = int(std::ceil(sx)) + 1 + ext + 3;
+  int bh = int(std::ceil(sy)) + 1 + ext;
+  bw = (bw + 3) & ~3;
+  P.box_w = bw;
+  P.box_h = bh;
+}
+
+int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
+               float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
+               int32_t h, int32_t order, uint32_t flags, double* coords, int ideg_override,
+               FwdPlan& P) {
+  int rc;
+  if ((rc = check_wcs(src, "source")) != DFR_OK) return rc;
+  if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
+  if (order < DFR_NEAREST || order > DFR_BICUBIC)
+    return fail(DFR_ERR_INVALID_ARG, "order must be DFR_NEAREST, DFR_BILINEAR or DFR_BICUBIC");
+  if (flags & ~(DFR_SPLIT | DFR_EXACT_INVERSE | DFR_NO_TMA))
+    return fail(DFR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
+  if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative output size");
+  if (w > 0 && h > 0) {
+    if (!img || !out) return fail(DFR_ERR_INVALID_ARG, "source image and output must be non-NULL");
+    if (pitch < src->naxis[0]) return fail(DFR_ERR_INVALID_ARG, "source pitch < NAXIS1");
+    if (out_pitch < w) return fail(DFR_ERR_INVALID_ARG, "output pitch < width");
+  }
+  const bool src_sip = src->a_order > 0 || src->b_order > 0;
+  const bool src_inv = src->ap_order > 0 || src->bp_order > 0;
+  const bool exact = (flags & DFR_EXACT_INVERSE) != 0;
+  if (src_sip && !src_inv && !exact)
+    return fail(DFR_ERR_NO_INVERSE_SIP,
+                "source has SIP A/B but no AP/BP: fit them (dfr_wcs_fit_inverse_sip) or pass "
+                "DFR_EXACT_INVERSE");
+
+  std::memset(&P, 0, sizeof(P));
+  P.x0 = x0;
+  P.y0 = y0;
+  P.w = w;
+  P.h = h;
+  P.tiles_x = (w + kTileW - 1) / kTileW;
+  P.tiles_y = (h + kTileH - 1) / kTileH;
+  P.out = out;
+  P.fp = fp;
+  P.out_pitch = out_pitch;
+  P.coords = coords;
+  P.img = img;
+  P.pitch = pitch;
+  P.W = src->naxis[0];
+  P.H = src->naxis[1];
+  P.flags = int32_t(flags);
+  P.order = order;
+  const bool tgt_sip = tgt->a_order > 0 || tgt->b_order > 0;
+  P.identity = same_linear(*src, *tgt) &&
+               ((!tgt_sip && !src_sip && !src_inv) || (exact && same_sip(*src, *tgt)));
+
+  // target
+  P.crpix_t[0] = tgt->crpix[0] - 1.0;
+  P.crpix_t[1] = tgt->crpix[1] - 1.0;
+  P.tsip_deg = std::max(tgt->a_order, tgt->b_order);
+  pack_poly(tgt->a, tgt->a_order, P.tsip_deg, P.tsip_d[0]);
+  pack_poly(tgt->b, tgt->b_order, P.tsip_deg, P.tsip_d[1]);
+  pack_poly(tgt->a, tgt->a_order, P.tsip_deg, P.tsip_f[0]);
+  pack_poly(tgt->b, tgt->b_order, P.tsip_deg, P.tsip_f[1]);
+  // source
+  P.crpix_s[0] = src->crpix[0] - 1.0;
+  P.crpix_s[1] = src->crpix[1] - 1.0;
+  P.isip_deg = ideg_override >= 0 ? ideg_override
+                                  : sip_round_degree(std::max(src->ap_order, src->bp_order));
+  pack_poly(src->ap, src->ap_order, P.isip_deg, P.isip_d[0]);
+  pack_poly(src->bp, src->bp_order, P.isip_deg, P.isip_d[1]);
+  pack_poly(src->ap, src->ap_order, P.isip_deg, P.isip_f[0]);
+  pack_poly(src->bp, src->bp_order, P.isip_deg, P.isip_f[1]);
+  P.fsip_deg = exact ? std::max(src->a_order, src->b_order) : 0;
+  pack_poly(src->a, src->a_order, std::max(P.fsip_deg, 0), P.fsip_d[0]);
+  pack_poly(src->b, src->b_order, std::max(P.fsip_deg, 0), P.fsip_d[1]);
+  pack_poly(src->a, src->a_order, std::max(P.fsip_deg, 0), P.fsip_f[0]);
+  pack_poly(src->b, src->b_order, std::max(P.fsip_deg, 0), P.fsip_f[1]);
+  P.newton_iters = src_inv ? 3 : 6;
+
+  // FP64 path constants (Sec. 3.2.1 / 3.2.2)
+  P.ra0_t = tgt->crval[0] * kDeg;
+  P.sd0_t = std::sin(tgt->crval[1] * kDeg);
+  P.cd0_t = std::cos(tgt->crval[1] * kDeg);
+  std::memcpy(P.cd_t, tgt->cd, sizeof(P.cd_t));
+  P.ra0_s = src->crval[0] * kDeg;
+  P.sd0_s = std::sin(src->crval[1] * kDeg);
+  P.cd0_s = std::cos(src->crval[1] * kDeg);
+  cd_inverse(src->cd, P.cdinv_s);
+
+  // Split path: TAN -> sky -> TAN is projective. With F = tangent frame (east, north, centre),
+  // a target standard coordinate (xi, eta) maps to F_s^T F_t (xi, eta, 1) in the source frame.
+  double Ft[3][3], Fs[3][3], K[3][3];
+  tangent_frame(tgt->crval[0], tgt->crval[1], Ft);
+  tangent_frame(src->crval[0], src->crval[1], Fs);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += Fs[k][i] * Ft[k][j];
+      K[i][j] = s;
+    }
+  // Mt: pixel offsets (p, q) -> (xi, eta, 1); Ms: (xi_s, eta_s, 1) -> (U, V, 1)
+  double Mt[3][3] = {{tgt->cd[0][0] / kR0, tgt->cd[0][1] / kR0, 0.0},
+                     {tgt->cd[1][0] / kR0, tgt->cd[1][1] / kR0, 0.0},
+                     {0.0, 0.0, 1.0}};
+  double Ms[3][3] = {{kR0 * P.cdinv_s[0][0], kR0 * P.cdinv_s[0][1], 0.0},
+                     {kR0 * P.cdinv_s[1][0], kR0 * P.cdinv_s[1][1], 0.0},
+                     {0.0, 0.0, 1.0}};
+  double KM[3][3], G[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += K[i][k] * Mt[k][j];
+      KM[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += Ms[i][k] * KM[k][j];
+      G[i][j] = s;
+    }
+  const double g22 = G[2][2];
+  if (!(g22 > 0.0))
+    return fail(DFR_ERR_UNSUPPORTED_WCS, "target and source tangent points are >= 90 deg apart");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) P.G[i][j] = G[i][j] / g22;
+
+  // TMA staging of the source tile (split path only)
+  P.use_tma = 0;
+  if ((flags & DFR_SPLIT) && !(flags & DFR_NO_TMA) && w > 0 && h > 0) {
+    size_box(P);
+    const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
+    const bool fits = P.box_w <= 256 && P.box_h <= 256 && P.box_w * P.box_h * 4 <= 64 * 1024;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (aligned && fits && enc) {
+      cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
+      cuuint64_t gstride[1] = {cuuint64_t(pitch) * 4};
+      cuuint32_t bdim[2] = {cuuint32_t(P.box_w), cuuint32_t(P.box_h)};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = enc(&P.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), gdim,
+                       gstride, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r == CUDA_SUCCESS) P.use_tma = 1;
+    }
+  }
+  return DFR_OK;
+}
+
+// Dynamic shared memory of a split launch: the source box plus 128 bytes of alignment slack.
+int smem_for(const FwdPlan& P) { return P.use_tma ? P.box_w * P.box_h * 4 + 128 : 0; }
+
+// ------------------------------------------------------------------------------ device ctx
+// Library-owned device memory and graphs for the batched path, per device.
+struct GraphKey {
+  int n, order, flags, ideg, grid, smem, nfp;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(n, order, flags, ideg, grid, smem, nfp) <
+           std::tie(o.n, o.order, o.flags, o.ideg, o.grid, o.smem, o.nfp);
+  }
+};
+
+struct DeviceCtx {
+  int device = -1;
+  int sms = 0;
+  size_t cap = 0;               // frames the buffers hold
+  FwdPlan* h_plans = nullptr;   // pinned
+  int32_t* h_starts = nullptr;  // pinned
+  FwdPlan* d_plans = nullptr;
+  int32_t* d_starts = nullptr;
+  int32_t* d_counter = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t done = nullptr;   // recorded after each batched launch (host buffers reusable)
+  bool pending = false;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tuned;  // -> (ctas/SM, tma)
+};
+
+std::mutex g_mu;
+std::map<int, DeviceCtx> g_ctx;
+
+int ensure_ctx(DeviceCtx*& out, size_t nframes) {
+  int dev = 0;
+  DFR_CUDA(cudaGetDevice(&dev));
+  DeviceCtx& c = g_ctx[dev];
+  if (c.device < 0) {
+    c.device = dev;
+    DFR_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+    DFR_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    DFR_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+  }
+  if (c.pending) {
+    DFR_CUDA(cudaEventSynchronize(c.done));
+    c.pending = false;
+  }
+  if (nframes > c.cap) {
+    for (auto& kv : c.graphs) cudaGraphExecDestroy(kv.second);
+    c.graphs.clear();
+    if (c.h_plans) cudaFreeHost(c.h_plans);
+    if (c.h_starts) cudaFreeHost(c.h_starts);
+    if (c.d_plans) cudaFree(c.d_plans);
+    if (c.d_starts) cudaFree(c.d_starts);
+    if (!c.d_counter) DFR_CUDA(cudaMalloc(&c.d_counter, 256));
+    size_t cap = std::max<size_t>(nframes, 64);
+    DFR_CUDA(cudaMallocHost(&c.h_plans, cap * sizeof(FwdPlan)));
+    DFR_CUDA(cudaMallocHost(&c.h_starts, (cap + 1) * sizeof(int32_t)));
+    DFR_CUDA(cudaMalloc(&c.d_plans, cap * sizeof(FwdPlan)));
+    DFR_CUDA(cudaMalloc(&c.d_starts, (cap + 1) * sizeof(int32_t)));
+    c.cap = cap;
+  }
+  out = &c;
+  return DFR_OK;
+}
+
+}  // namespace
+}  // namespace dfr
+
+using namespace dfr;
+
+// ================================================================================== C ABI
+extern "C" {
+
+const char* dfr_last_error(void) { return g_err.c_str(); }
+
+int dfr_abi_version(void) { return DFR_ABI_VERSION; }
+
+int dfr_wcs_from_header(const char* cards, size_t nbytes, dfr_wcs* out) {
+  if (!cards || !out) return fail(DFR_ERR_INVALID_ARG, "NULL argument");
+  std::string text(cards, nbytes);
+  std::vector<std::string> recs;
+  if (text.find('\n') != std::string::npos) {
+    size_t s = 0;
+    while (s <= text.size()) {
+      size_t e = text.find('\n', s);
+      if (e == std::string::npos) e = text.size();
+      std::string r = text.substr(s, e - s);
+      if (!r.empty() && r.back() == '\r') r.pop_back();
+      recs.push_back(r);
+      s = e + 1;
+    }
+  } else {
+    for (size_t s = 0; s < text.size(); s += 80) recs.push_back(text.substr(s, 80));
+  }
+  std::map<std::string, Card> kv;
+  for (const std::string& r : recs) {
+    std::string key = trim(r.substr(0, std::min<size_t>(8, r.size())));
+    if (key.empty() || key == "END" || key == "COMMENT" || key == "HISTORY") continue;
+    if (r.size() < 10 || r[8] != '=' || r[9] != ' ') continue;
+    Card c;
+    if (!parse_value(r.substr(10), c))
+      return fail(DFR_ERR_HEADER_PARSE, "cannot parse value of %s", key.c_str());
+    kv[key] = c;
+  }
+  auto num = [&](const char* k, double& v) -> bool {
+    auto it = kv.find(k);
+    if (it == kv.end() || it->second.is_str) return false;
+    v = it->second.d;
+    return true;
+  };
+  auto str = [&](const char* k, std::string& v) -> bool {
+    auto it = kv.find(k);
+    if (it == kv.end() || !it->second.is_str) return false;
+    v = it->second.s;
+    return true;
+  };
+  dfr_wcs w;
+  std::memset(&w, 0, sizeof(w));
+  double n1, n2;
+  std::string c1, c2;
+  if (!num("NAXIS1", n1) || !num("NAXIS2", n2))
+    return fail(DFR_ERR_HEADER_PARSE, "missing NAXIS1/NAXIS2");
+  if (!str("CTYPE1", c1) || !str("CTYPE2", c2))
+    return fail(DFR_ERR_HEADER_PARSE, "missing CTYPE1/CTYPE2");
+  if (!num("CRPIX1", w.crpix[0]) || !num("CRPIX2", w.crpix[1]))
+    return fail(DFR_ERR_HEADER_PARSE, "missing CRPIX1/CRPIX2");
+  if (!num("CRVAL1", w.crval[0]) || !num("CRVAL2", w.crval[1]))
+    return fail(DFR_ERR_HEADER_PARSE, "missing CRVAL1/CRVAL2");
+  auto tan_ok = [](const std::string& c, const char* base) {
+    return c.compare(0, 8, base) == 0 && (c.size() == 8 || c.substr(8) == "-SIP");
+  };
+  if (!tan_ok(c1, "RA---TAN") || !tan_ok(c2, "DEC--TAN"))
+    return fail(DFR_ERR_UNSUPPORTED_WCS, "CTYPE %s/%s: only RA---TAN/DEC--TAN[-SIP]", c1.c_str(),
+                c2.c_str());
+  double lonpole;
+  if (num("LONPOLE", lonpole) && lonpole != 180.0)
+    return fail(DFR_ERR_UNSUPPORTED_WCS, "LONPOLE %g: only 180 is supported", lonpole);
+  w.naxis[0] = int32_t(n1);
+  w.naxis[1] = int32_t(n2);
+  const bool has_cd = kv.count("CD1_1") || kv.count("CD1_2") || kv.count("CD2_1") ||
+                      kv.count("CD2_2");
+  if (has_cd) {
+    const char* ks[2][2] = {{"CD1_1", "CD1_2"}, {"CD2_1", "CD2_2"}};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        double v = 0.0;
+        num(ks[i][j], v);
+        w.cd[i][j] = v;
+      }
+  } else {
+    double d1, d2;
+    if (!num("CDELT1", d1) || !num("CDELT2", d2))
+      return fail(DFR_ERR_HEADER_PARSE, "no CDi_j and no CDELT1/CDELT2");
+    double pc[2][2] = {{1.0, 0.0}, {0.0, 1.0}};
+    const char* ks[2][2] = {{"PC1_1", "PC1_2"}, {"PC2_1", "PC2_2"}};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) num(ks[i][j], pc[i][j]);
+    const double d[2] = {d1, d2};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) w.cd[i][j] = d[i] * pc[i][j];
+  }
+  const double det = w.cd[0][0] * w.cd[1][1] - w.cd[0][1] * w.cd[1][0];
+  if (!(det != 0.0) || !std::isfinite(det)) return fail(DFR_ERR_SINGULAR_CD, "CD is singular");
+  struct {
+    const char* name;
+    int32_t* order;
+    double (*c)[10];
+  } polys[4] = {{"A", &w.a_order, w.a}, {"B", &w.b_order, w.b}, {"AP", &w.ap_order, w.ap},
+                {"BP", &w.bp_order, w.bp}};
+  for (auto& pl : polys) {
+    double o = 0.0;
+    std::string ok = std::string(pl.name) + "_ORDER";
+    if (num(ok.c_str(), o)) {
+      if (o < 0 || o > DFR_MAX_SIP || o != std::floor(o))
+        return fail(DFR_ERR_HEADER_PARSE, "%s out of range", ok.c_str());
+      *pl.order = int32_t(o);
+    }
+    const std::string pfx = std::string(pl.name) + "_";
+    for (auto& e : kv) {
+      int p, q;
+      if (!sip_name(e.first, pfx.c_str(), p, q)) continue;
+      if (e.second.is_str) return fail(DFR_ERR_HEADER_PARSE, "%s is not a number", e.first.c_str());
+      if (p >= 0 && q >= 0 && p + q >= 1 && p + q <= *pl.order) pl.c[p][q] = e.second.d;
+    }
+  }
+  if (!finite_wcs(w)) return fail(DFR_ERR_HEADER_PARSE, "non-finite WCS value");
+  *out = w;
+  return DFR_OK;
+}
+
+int dfr_wcs_fit_inverse_sip(dfr_wcs* wcs, int32_t order, double* max_resid_px,
+                            double* rms_resid_px) {
+  if (!wcs) return fail(DFR_ERR_INVALID_ARG, "NULL WCS");
+  if (order < 1 || order > DFR_MAX_SIP) return fail(DFR_ERR_INVALID_ARG, "order must be 1..9");
+  int rc = check_wcs(wcs, "input");
+  if (rc != DFR_OK) return rc;
+  const int W = wcs->naxis[0], H = wcs->naxis[1];
+  const double R = 0.5 * std::max(W, H);
+  const int ng = 100;
+  const double margin = 0.05;
+  std::vector<std::pair<int, int>> terms;
+  for (int n = 1; n <= order; ++n)
+    for (int p = n; p >= 0; --p) terms.push_back({p, n - p});
+  const int m = ng * ng, k = int(terms.size());
+  std::vector<double> A(size_t(m) * k), bu(m), bv(m);
+  for (int j = 0; j < ng; ++j)
+    for (int i = 0; i < ng; ++i) {
+      const double x = -margin * W - 0.5 + ((1.0 + 2 * margin) * W) * i / (ng - 1);
+      const double y = -margin * H - 0.5 + ((1.0 + 2 * margin) * H) * j / (ng - 1);
+      const double u = x - (wcs->crpix[0] - 1.0), v = y - (wcs->crpix[1] - 1.0);
+      const double U = u + poly_eval(wcs->a, wcs->a_order, u, v);
+      const double V = v + poly_eval(wcs->b, wcs->b_order, u, v);
+      const int r = j * ng + i;
+      for (int t = 0; t < k; ++t)
+        A[size_t(t) * m + r] = std::pow(U / R, terms[t].first) * std::pow(V / R, terms[t].second);
+      bu[r] = u - U;
+      bv[r] = v - V;
+    }
+  // Householder QR of the column-major m x k matrix, applied to both right-hand sides
+  for (int c = 0; c < k; ++c) {
+    double* col = &A[size_t(c) * m];
+    double nrm = 0.0;
+    for (int r = c; r < m; ++r) nrm += col[r] * col[r];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) return fail(DFR_ERR_INVALID_ARG, "degenerate inverse-SIP fit");
+    const double alpha = col[c] > 0 ? -nrm : nrm;
+    std::vector<double> vh(m - c);
+    for (int r = c; r < m; ++r) vh[r - c] = col[r];
+    vh[0] -= alpha;
+    double vn = 0.0;
+    for (double t : vh) vn += t * t;
+    if (vn == 0.0) continue;
+    auto apply = [&](double* y) {
+      double s = 0.0;
+      for (int r = c; r < m; ++r) s += vh[r - c] * y[r];
+      s = 2.0 * s / vn;
+      for (int r = c; r < m; ++r) y[r] -= s * vh[r - c];
+    };
+    for (int c2 = c; c2 < k; ++c2) apply(&A[size_t(c2) * m]);
+    apply(bu.data());
+    apply(bv.data());
+  }
+  std::vector<double> xu(k), xv(k);
+  for (int c = k - 1; c >= 0; --c) {
+    double su = bu[c], sv = bv[c];
+    for (int c2 = c + 1; c2 < k; ++c2) {
+      su -= A[size_t(c2) * m + c] * xu[c2];
+      sv -= A[size_t(c2) * m + c] * xv[c2];
+    }
+    xu[c] = su / A[size_t(c) * m + c];
+    xv[c] = sv / A[size_t(c) * m + c];
+  }
+  std::memset(wcs->ap, 0, sizeof(wcs->ap));
+  std::memset(wcs->bp, 0, sizeof(wcs->bp));
+  for (int t = 0; t < k; ++t) {
+    const int p = terms[t].first, q = terms[t].second;
+    wcs->ap[p][q] = xu[t] / std::pow(R, p + q);
+    wcs->bp[p][q] = xv[t] / std::pow(R, p + q);
+  }
+  wcs->ap_order = wcs->bp_order = order;
+  if (max_resid_px || rms_resid_px) {
+    const int nc = 512;
+    double mx = 0.0, ss = 0.0;
+    for (int j = 0; j < nc; ++j)
+      for (int i = 0; i < nc; ++i) {
+        const double x = -0.5 + double(W) * i / (nc - 1), y = -0.5 + double(H) * j / (nc - 1);
+        const double u = x - (wcs->crpix[0] - 1.0), v = y - (wcs->crpix[1] - 1.0);
+        const double U = u + poly_eval(wcs->a, wcs->a_order, u, v);
+        const double V = v + poly_eval(wcs->b, wcs->b_order, u, v);
+        const double ru = U + poly_eval(wcs->ap, order, U, V) - u;
+        const double rv = V + poly_eval(wcs->bp, order, U, V) - v;
+        const double r = std::hypot(ru, rv);
+        mx = std::max(mx, r);
+        ss += r * r;
+      }
+    if (max_resid_px) *max_resid_px = mx;
+    if (rms_resid_px) *rms_resid_px = std::sqrt(ss / (double(nc) * nc));
+  }
+  return DFR_OK;
+}
+
+int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]) {
+  if (!bbox) return fail(DFR_ERR_INVALID_ARG, "NULL bbox");
+  int rc;
+  if ((rc = check_wcs(src, "source")) != DFR_OK) return rc;
+  if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
+  // Reverse map: source boundary pixel -> sky (source WCS) -> target pixel (target WCS), in
+  // FP64, through the same projective form as the split plan with the roles swapped.
+  FwdPlan P;
+  dfr_wcs s2 = *tgt, t2 = *src;  // map source pixels into target pixels
+  const bool t_sip = s2.a_order > 0 || s2.b_order > 0;
+  if (t_sip && !(s2.ap_order > 0 || s2.bp_order > 0)) {
+    rc = dfr_wcs_fit_inverse_sip(&s2, std::min(DFR_MAX_SIP, std::max(s2.a_order, s2.b_order) + 1),
+                                 nullptr, nullptr);
+    if (rc != DFR_OK) return rc;
+  }
+  if (t2.a_order > 0 || t2.b_order > 0) {
+    t2.ap_order = t2.bp_order = 0;
+  }
+  rc = build_plan(&s2, &t2, nullptr, 0, nullptr, nullptr, 0, 0, 0, 0, 0, DFR_BILINEAR, DFR_SPLIT,
+                  nullptr, -1, P);
+  if (rc != DFR_OK) return rc;
+  HostMap M{&P};
+  const int W = src->naxis[0], H = src->naxis[1];
+  const int ns = 256;
+  double xmn = 1e300, xmx = -1e300, ymn = 1e300, ymx = -1e300;
+  int hits = 0;
+  for (int e = 0; e < 4; ++e)
+    for (int i = 0; i <= ns; ++i) {
+      const double t = double(i) / ns;
+      double X, Y;
+      switch (e) {
+        case 0: X = -0.5 + t * W; Y = -0.5; break;
+        case 1: X = W - 0.5; Y = -0.5 + t * H; break;
+        case 2: X = -0.5 + t * W; Y = H - 0.5; break;
+        default: X = -0.5; Y = -0.5 + t * H; break;
+      }
+      double xs, ys;
+      if (!M.eval(X, Y, xs, ys)) continue;
+      xmn = std::min(xmn, xs);
+      xmx = std::max(xmx, xs);
+      ymn = std::min(ymn, ys);
+      ymx = std::max(ymx, ys);
+      ++hits;
+    }
+  bbox[0] = bbox[1] = bbox[2] = bbox[3] = 0;
+  if (!hits) return DFR_OK;
+  const int TW = tgt->naxis[0], TH = tgt->naxis[1];
+  const double margin = 2.0;
+  const long x0 = std::max<long>(0, long(std::floor(xmn - margin)));
+  const long y0 = std::max<long>(0, long(std::floor(ymn - margin)));
+  const long x1 = std::min<long>(TW - 1, long(std::ceil(xmx + margin)));
+  const long y1 = std::min<long>(TH - 1, long(std::ceil(ymx + margin)));
+  if (x1 < x0 || y1 < y0) return DFR_OK;
+  bbox[0] = int32_t(x0);
+  bbox[1] = int32_t(y0);
+  bbox[2] = int32_t(x1 - x0 + 1);
+  bbox[3] = int32_t(y1 - y0 + 1);
+  return DFR_OK;
+}
+
+int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
+                  int64_t src_pitch, float* out, float* footprint, int64_t out_pitch, int32_t x0,
+                  int32_t y0, int32_t out_w, int32_t out_h, int32_t order, uint32_t flags,
+                  double* coords_out, void* stream) {
+  FwdPlan P;
+  int rc = build_plan(src, tgt, src_img, src_pitch, out, footprint, out_pitch, x0, y0, out_w,
+                      out_h, order, flags, coords_out, -1, P);
+  if (rc != DFR_OK) return rc;
+  if (out_w == 0 || out_h == 0) return DFR_OK;
+  FwdLaunch L{};
+  L.total_tiles = P.tiles_x * P.tiles_y;
+  cudaError_t e = launch_forward(P, L, L.total_tiles, forward_threads_default(), smem_for(P),
+                                 static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject launch");
+  return DFR_OK;
+}
+
+int dfr_num_params(const dfr_wcs* src) {
+  if (!src) return fail(DFR_ERR_INVALID_ARG, "NULL WCS");
+  auto nterms = [](int o) { return o <= 0 ? 0 : (o + 1) * (o + 2) / 2 - 1; };
+  return 6 + nterms(src->a_order) + nterms(src->b_order);
+}
+
+int dfr_device_status(void* stream) {
+  int32_t a = 0, b = 0;
+  cudaError_t e = read_and_clear_status_fwd(&a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  e = read_and_clear_status_bwd(&b, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  const int32_t s = a | b;
+  if (s & kStatusTimeout) return fail(DFR_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (s & kStatusCheck) return fail(DFR_ERR_DEVICE, "a kernel reported a failed check");
+  return DFR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool autotune_enabled() {
+  const char* e = std::getenv("DFR_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+// Upload the frame table, zero the work counter and launch the persistent kernel.
+cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int smem, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c.d_plans, c.h_plans, size_t(n) * sizeof(FwdPlan),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(c.d_starts, c.h_starts, size_t(n + 1) * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(c.d_counter, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  FwdLaunch L{};
+  L.plans = c.d_plans;
+  L.tile_start = c.d_starts;
+  L.nframes = n;
+  L.counter = c.d_counter;
+  return launch_forward(c.h_plans[0], L, grid, forward_threads_default(), smem, s);
+}
+
+// Tile-launch autotuner: CTAs per SM of the persistent grid and TMA staging on/off, timed on
+// the caller's data (outputs are rewritten identically by every candidate).
+std::pair<int, int> autotune(DeviceCtx& c, int n, int smem, int total, cudaStream_t s) {
+  const int threads = forward_threads_default();
+  const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
+  std::vector<std::pair<int, int>> cand;
+  for (int k : {1, 2, 3, 4, 6, 8})
+    if (k <= maxb) cand.push_back({k, smem > 0 ? 1 : 0});
+  if (smem > 0) {
+    const int maxb0 = forward_max_blocks_per_sm(c.h_plans[0], threads, 0);
+    for (int k : {2, 4, 8})
+      if (k <= maxb0) cand.push_back({k, 0});
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<FwdPlan> saved(c.h_plans, c.h_plans + n);
+  float best = 1e30f;
+  std::pair<int, int> pick = cand.empty() ? std::make_pair(1, 0) : cand[0];
+  for (auto cd : cand) {
+    for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = cd.second ? saved[f].use_tma : 0;
+    const int sm = cd.second ? smem : 0;
+    const int grid = std::max(1, std::min(total, c.sms * cd.first));
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s);
+      ok = enqueue_batch(c, n, grid, sm, s) == cudaSuccess;
+    }
+    cudaEventRecord(e1, s);
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = cd;
+    }
+  }
+  std::copy(saved.begin(), saved.end(), c.h_plans);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  return pick;
+}
+
+}  // namespace
+
+extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
+                                   int32_t order, uint32_t flags, void* stream) {
+  if (n < 0) return fail(DFR_ERR_INVALID_ARG, "negative frame count");
+  if (n == 0) return DFR_OK;
+  if (!frames) return fail(DFR_ERR_INVALID_ARG, "NULL frame array");
+  if (n > (1 << 20)) return fail(DFR_ERR_INVALID_ARG, "too many frames");
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCtx* cp = nullptr;
+  int rc = ensure_ctx(cp, size_t(n));
+  if (rc != DFR_OK) return rc;
+  DeviceCtx& c = *cp;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int ideg = 0;
+  for (int f = 0; f < n; ++f)
+    ideg = std::max(ideg, sip_round_degree(std::max(frames[f].wcs.ap_order, frames[f].wcs.bp_order)));
+  int64_t total = 0;
+  int smem = 0;
+  for (int f = 0; f < n; ++f) {
+    const dfr_frame& fr = frames[f];
+    rc = build_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
+                    fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, c.h_plans[f]);
+    if (rc != DFR_OK) {
+      g_err = "frame " + std::to_string(f) + ": " + g_err;
+      return rc;
+    }
+    c.h_starts[f] = int32_t(total);
+    if (fr.w > 0 && fr.h > 0) total += int64_t(c.h_plans[f].tiles_x) * c.h_plans[f].tiles_y;
+    smem = std::max(smem, smem_for(c.h_plans[f]));
+  }
+  if (total >= (int64_t(1) << 31)) return fail(DFR_ERR_INVALID_ARG, "batch too large");
+  c.h_starts[n] = int32_t(total);
+  if (total == 0) return DFR_OK;
+
+  const auto tkey = std::make_tuple(order, int(flags), ideg, 31 - __builtin_clz(unsigned(n)));
+  auto it = c.tuned.find(tkey);
+  std::pair<int, int> cfg;
+  if (it != c.tuned.end()) {
+    cfg = it->second;
+  } else if (autotune_enabled()) {
+    cfg = autotune(c, n, smem, int(total), s);
+    c.tuned[tkey] = cfg;
+  } else {
+    cfg = {std::min(4, forward_max_blocks_per_sm(c.h_plans[0], forward_threads_default(), smem)),
+           smem > 0 ? 1 : 0};
+  }
+  if (!cfg.second) {
+    for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = 0;
+    smem = 0;
+  }
+  const int grid = std::max(1, std::min(int(total), c.sms * cfg.first));
+  GraphKey gk{n, order, int(flags), ideg, grid, smem, 0};
+  auto g = c.graphs.find(gk);
+  if (g == c.graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    DFR_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_batch(c, n, grid, smem, c.cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(c.cap_stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    g = c.graphs.emplace(gk, exec).first;
+  }
+  DFR_CUDA(cudaGraphLaunch(g->second, s));
+  DFR_CUDA(cudaEventRecord(c.done, s));
+  c.pending = true;
+  return DFR_OK;
+}
+
+extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
+                                      const float* src_img, int64_t src_pitch,
+                                      const float* grad_out, int64_t go_pitch, int32_t x0,
+                                      int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
+                                      uint32_t flags, float* grad_src, int64_t gs_pitch,
+                                      double* grad_params, void* stream) {
+  (void)src; (void)tgt; (void)src_img; (void)src_pitch; (void)grad_out; (void)go_pitch;
+  (void)x0; (void)y0; (void)out_w; (void)out_h; (void)order; (void)flags; (void)grad_src;
+  (void)gs_pitch; (void)grad_params; (void)stream;
+  return fail(DFR_ERR_INVALID_ARG, "backward not built yet");
+}

@@ -1,0 +1,107 @@
+// Internal plan structures shared by the host plan builder (dfr_host.cpp) and the kernels
+// (dfr_fwd.cu, dfr_bwd.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dfr.h"
+
+namespace dfr {
+
+// Coefficients of a 2-D polynomial of total degree <= N, packed row by row in p:
+// P(u, v) = sum_p u^p C_p(v), C_p(v) = sum_{q <= N-p} c[off(p) + q] v^q, off(p) = p(N+1) - p(p-1)/2.
+// The constant term c[0] is always 0 (SIP has no constant term).
+constexpr int kMaxCoef = (DFR_MAX_SIP + 1) * (DFR_MAX_SIP + 2) / 2;  // 55
+
+__host__ __device__ constexpr int poly_off(int p, int n) { return p * (n + 1) - p * (p - 1) / 2; }
+__host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) / 2; }
+
+// Target tile (the unit of work and the anchor cell of the split path): 64 x 16 pixels,
+// relative to the bounding-box origin.
+constexpr int kTileW = 64;
+constexpr int kTileH = 16;
+constexpr int kTilePix = kTileW * kTileH;
+
+// Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
+struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requires
+  CUtensorMap tmap;          // source image tile map (valid when use_tma != 0)
+  // target bounding box and its tiling
+  int32_t x0, y0, w, h;
+  int32_t tiles_x, tiles_y;
+  // outputs (device)
+  float* out;
+  float* fp;                 // nullable
+  int64_t out_pitch;
+  double* coords;            // nullable: 2 doubles per output pixel
+  // source image (device)
+  const float* img;
+  int64_t pitch;
+  int32_t W, H;
+  int32_t use_tma, box_w, box_h;
+  int32_t identity;          // source and target WCS are bitwise equal
+  // target WCS
+  double crpix_t[2];         // CRPIX - 1 (0-based reference pixel)
+  int32_t tsip_deg;          // 0 = no target SIP; else packed degree of A, B
+  double tsip_d[2][kMaxCoef];
+  float tsip_f[2][kMaxCoef];
+  // split path: homography from target intermediate offsets (p, q) (after SIP, pixels) to
+  // source intermediate offsets (U, V) (before inverse SIP, pixels), scaled so G[2][2] = 1
+  double G[3][3];
+  // source WCS
+  double crpix_s[2];         // CRPIX - 1
+  int32_t isip_deg;          // packed degree of AP, BP (0 = none)
+  float isip_f[2][kMaxCoef];
+  double isip_d[2][kMaxCoef];
+  int32_t fsip_deg;          // packed degree of the source A, B (exact inverse; 0 = none)
+  float fsip_f[2][kMaxCoef];
+  double fsip_d[2][kMaxCoef];
+  int32_t newton_iters;      // FP32 Newton steps in the split exact inverse
+  // all-FP64 path constants
+  double ra0_t, sd0_t, cd0_t;
+  double cd_t[2][2];
+  double ra0_s, sd0_s, cd0_s;
+  double cdinv_s[2][2];
+  int32_t flags;
+  int32_t order;
+};
+
+// Launch description shared by the forward kernels.
+struct FwdLaunch {
+  const FwdPlan* plans;      // batch: device array of n plans (nullptr: single frame in p0)
+  const int32_t* tile_start; // batch: device prefix sums of tiles per frame (n + 1 entries;
+                             // the last is the total tile count)
+  int32_t nframes;
+  int32_t total_tiles;       // single frame: tiles in the grid (batch reads tile_start[n])
+  int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
+  int32_t smem_box_floats;   // dynamic shared memory reserved for the source box
+};
+
+// Backward plan extras (parameter layout of dfr_reproject_backward).
+struct BwdExtra {
+  float* grad_src;
+  int64_t gs_pitch;
+  const float* grad_out;
+  int64_t go_pitch;
+  double* grad_params;       // final (nparams)
+  double* partials;          // scratch: nblocks x nparams
+  int32_t nparams;
+  int32_t na, nb;            // number of A and B terms
+  int32_t a_deg, b_deg;      // source A/B orders (for the parameter monomials)
+};
+
+// Device status word: bit 0 = a bounded wait timed out, bit 1 = internal check failed.
+enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
+
+// Kernel launchers (dfr_fwd.cu / dfr_bwd.cu). Return cudaError_t.
+cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
+                           int smem_bytes, cudaStream_t s);
+const void* forward_kernel(const FwdPlan& p0);
+int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
+int forward_threads_default();
+cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
+cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
+
+}  // namespace dfr

@@ -1,0 +1,205 @@
+"""GPU parity of dfr_reproject with the FP64 oracle (element by element), through the C ABI.
+
+Criteria (derived from the 1e-3 px / 1e-5 relative targets):
+  * source coordinates: all-FP64 path within 1e-8 px of the oracle, split path within 1e-3 px;
+  * values: the oracle interpolates at the GPU's own emitted coordinates (same coverage
+    decisions, taken on the same numbers) and |gpu - oracle| <= 1e-5 * max(|oracle|, 1);
+  * end to end (oracle coordinates) the FP64 path meets the same 1e-5 bound.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reproject as OR
+from oracle import wcs as OW
+
+from gpu_util import (FP64_PX, SPLIT_PX, VALUE_RTOL, coord_check, dfr, gpu, to_dev, torch,
+                      value_check, with_inverse)
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_sip(order="bicubic", w=700, h=450, seed=7, tgt_rot=1.2, scale=1.01,
+               shift=(41.3, -17.9), sip_order=3, inv_order=4):
+    rng = synth.rng_for(seed)
+    src = synth.add_sip(synth.tan_wcs(w, h), sip_order, 1e-6, rng)
+    src, _ = OW.with_inverse_sip(src, inv_order)
+    tgt = synth.tan_wcs(w + 37, h - 21, scale_arcsec=2.5 * scale, rho_deg=tgt_rot,
+                        crpix=(src["crpix"][0] + shift[0], src["crpix"][1] + shift[1]))
+    img = synth.sky_image(w, h, synth.sources_for_area(w, h, 6000), rng)
+    return src, tgt, img
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_config0_full(precision):
+    c = synth.config0()
+    src, tgt, img = c["src"][0], c["tgt"], c["images"][0]
+    bbox = (0, 0, 512, 512)
+    val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", precision, bbox)
+    dmax, _ = coord_check(src, tgt, cr, bbox)
+    assert dmax < (FP64_PX if precision == "fp64" else SPLIT_PX)
+    e, fe = value_check(img, "bilinear", val, fp, cr, precision)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    if precision == "fp64":
+        ov, ofp, _, _ = OR.reproject(src, tgt, img, "bilinear")
+        err = np.abs(val - ov) / np.maximum(np.abs(ov), 1.0)
+        assert err.max() <= VALUE_RTOL
+        assert np.abs(fp - ofp).max() <= 1e-6
+
+
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_sip_ragged_tiles(order, precision):
+    src, tgt, img = _small_sip()
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    val, fp, cr = gpu(src, tgt, to_dev(img), order, precision, bbox)
+    dmax, _ = coord_check(src, tgt, cr, bbox)
+    assert dmax < (FP64_PX if precision == "fp64" else SPLIT_PX)
+    e, fe = value_check(img, order, val, fp, cr, precision)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    assert (fp == 0).any() and (fp > 0).mean() > 0.8  # partial coverage exercised
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_bbox_offset_pitch_and_degenerate_shapes(precision):
+    src, tgt, img = _small_sip(order="bilinear", w=300, h=200)
+    big = np.zeros((200, 320), np.float32)
+    big[:, :300] = img
+    img_d = to_dev(big)[:, :300]  # source pitch 320 > NAXIS1
+    T = torch()
+    for bbox in [(13, 7, 150, 77), (0, 0, 1, 1), (5, 9, 1, 120), (2, 3, 200, 1), (250, 150, 90, 70)]:
+        x0, y0, w, h = bbox
+        out = T.full((h, w + 5), -7.0, device="cuda")[:, :w]
+        fp = T.full((h, w + 5), -7.0, device="cuda")[:, :w]
+        val, fpv = dfr().reproject(img_d, src, tgt, bbox=bbox, order="bilinear",
+                                   precision=precision, out=out, fp_out=fp)
+        v2, f2, cr = gpu(src, tgt, to_dev(img), "bilinear", precision, bbox)
+        T.cuda.synchronize()
+        assert np.array_equal(val.cpu().numpy(), v2) and np.array_equal(fpv.cpu().numpy(), f2)
+        e, fe = value_check(img, "bilinear", v2, f2, cr, precision)
+        assert e <= VALUE_RTOL and fe <= 1e-6
+
+
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_identity_is_bit_exact(order, precision):
+    c = synth.config0()
+    src, img = c["src"][0], c["images"][0]
+    val, fp, _ = gpu(src, src, to_dev(img), order, precision, (0, 0, 512, 512))
+    assert np.array_equal(val, img) and np.all(fp == 1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_integer_shift_nearest_bit_exact(precision):
+    c = synth.config0()
+    src, img = c["src"][0], c["images"][0]
+    tgt = synth.copy_wcs(src)
+    tgt["crpix"] = (src["crpix"][0] + 5.0, src["crpix"][1] - 3.0)
+    val, fp, _ = gpu(src, tgt, to_dev(img), "nearest", precision, (0, 0, 512, 512))
+    exp = np.zeros_like(img)
+    exp[:509, 5:] = img[3:, :507]
+    assert np.array_equal(val, exp)
+    assert set(np.unique(fp)) <= {0.0, 1.0}
+
+
+def test_linear_ramp_bilinear_and_quadratic_bicubic():
+    c = synth.config0()
+    src, tgt = c["src"][0], c["tgt"]
+    Y, X = np.mgrid[0:512, 0:512].astype(np.float64)
+    ramp = (0.01 * X - 0.02 * Y + 3.0).astype(np.float32)
+    quad = (1e-4 * X * X - 2e-4 * X * Y + 5e-5 * Y * Y + 0.01 * X + 1.0).astype(np.float32)
+    for img, order in ((ramp, "bilinear"), (quad, "bicubic")):
+        for precision in ("fp64", "split"):
+            val, fp, cr = gpu(src, tgt, to_dev(img), order, precision, (0, 0, 512, 512))
+            x, y = cr[..., 0], cr[..., 1]
+            inner = (x > 2) & (x < 509) & (y > 2) & (y < 509)
+            if order == "bilinear":
+                exact = 0.01 * x - 0.02 * y + 3.0
+            else:
+                exact = 1e-4 * x * x - 2e-4 * x * y + 5e-5 * y * y + 0.01 * x + 1.0
+            # float32 source rounding bounds the reproduction, ~1e-6 of the image range
+            assert np.abs(val - exact)[inner].max() <= 1e-6 * np.abs(img).max() + 4e-7 * 8
+
+
+def test_tma_and_direct_gather_agree_bitwise():
+    src, tgt, img = _small_sip()
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    for order in ("nearest", "bilinear", "bicubic"):
+        a = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=True)
+        b = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=False)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v, equal_nan=True)
+
+
+def test_split_vs_fp64_coordinates():
+    src, tgt, img = _small_sip()
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    _, _, c64 = gpu(src, tgt, to_dev(img), "bicubic", "fp64", bbox)
+    _, _, c32 = gpu(src, tgt, to_dev(img), "bicubic", "split", bbox)
+    d = np.hypot(c64[..., 0] - c32[..., 0], c64[..., 1] - c32[..., 1])
+    assert np.nanmax(d) < SPLIT_PX
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_exact_inverse_newton(precision):
+    src, tgt, img = _small_sip(order="bilinear", w=400, h=300)
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", precision, bbox, exact=True)
+    dmax, _ = coord_check(src, tgt, cr, bbox, inverse="newton")
+    assert dmax < (FP64_PX if precision == "fp64" else SPLIT_PX)
+    e, fe = value_check(img, "bilinear", val, fp, cr, precision)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+
+
+def test_far_tangent_points_and_target_sip():
+    """Different CRVAL (projective map), a SIP target grid, and a target partly off the source."""
+    rng = synth.rng_for(99)
+    src = synth.add_sip(synth.tan_wcs(500, 400, crval=(150.0, 30.0)), 3, 1e-6, rng)
+    src, _ = OW.with_inverse_sip(src, 4)
+    tgt = synth.add_sip(synth.tan_wcs(520, 380, crval=(150.05, 30.04), rho_deg=-2.0,
+                                      scale_arcsec=2.7), 2, 1e-6, rng)
+    img = synth.sky_image(500, 400, 40, rng)
+    bbox = (0, 0, 520, 380)
+    for precision in ("fp64", "split"):
+        val, fp, cr = gpu(src, tgt, to_dev(img), "bicubic", precision, bbox)
+        dmax, _ = coord_check(src, tgt, cr, bbox)
+        assert dmax < (FP64_PX if precision == "fp64" else SPLIT_PX)
+        e, fe = value_check(img, "bicubic", val, fp, cr, precision)
+        assert e <= VALUE_RTOL and fe <= 1e-6
+
+
+def test_source_far_hemisphere_is_uncovered():
+    """A target grid spanning >90 deg: pixels whose sky position is on the far side of the source
+    projection are uncovered. The FP64 path decides per pixel exactly like the oracle; the split
+    path (FP64 anchor per 64x16 tile) never covers such a pixel."""
+    src = synth.tan_wcs(64, 64, crval=(0.0, 0.0))
+    tgt = synth.tan_wcs(64, 64, crval=(0.0, 0.0), scale_arcsec=3600.0 * 4)  # 4 deg/px
+    img = np.ones((64, 64), np.float32)
+    X, Y = np.meshgrid(np.arange(64.0), np.arange(64.0))
+    _, _, ok = OR.coords(src, tgt, X, Y)
+    assert (~ok).any()
+    val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", "fp64", (0, 0, 64, 64))
+    assert np.array_equal(np.isfinite(cr[..., 0]), ok)
+    val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", "split", (0, 0, 64, 64))
+    assert np.all(fp[~ok] == 0) and np.all(val[~ok] == 0)
+
+
+def test_config1_full_size_sampled():
+    """The bench workload (4096^2 TAN-SIP 3, bicubic, split) in its bench launch form, checked
+    on 20000 sampled pixels: coordinates vs the oracle and values at the GPU coordinates."""
+    c = synth.config1()
+    src = with_inverse(c)
+    tgt, img = c["tgt"], c["images"][0]
+    img_d = to_dev(img)
+    bbox = (0, 0, 4096, 4096)
+    val, fp, cr = gpu(src, tgt, img_d, "bicubic", "split", bbox)
+    rng = synth.rng_for(2024)
+    dmax, drms = coord_check(src, tgt, cr, bbox, sample=20000, rng=rng)
+    assert dmax < SPLIT_PX
+    idx = rng.integers(0, 4096 * 4096, 20000)
+    sel = (idx // 4096, idx % 4096)
+    e, fe = value_check(img, "bicubic", val[sel][None], fp[sel][None], cr[sel][None], "split")
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    # the bench call (no coordinate output) writes the same values
+    v2, f2 = dfr().reproject(img_d, src, tgt, bbox=bbox, order="bicubic", precision="split")
+    assert np.array_equal(v2.cpu().numpy(), val) and np.array_equal(f2.cpu().numpy(), fp)
