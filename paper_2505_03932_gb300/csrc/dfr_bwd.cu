@@ -1,7 +1,335 @@
-// Adjoint (backward) kernels: see dfr_reproject_backward in include/dfr.h.
+// Adjoint of the reprojection (dfr_reproject_backward), sm_103a.
+//
+// For value = N / F with N = sum_k w_k S_k and F = sum_k w_k over in-bounds taps (Sec. 3.1
+// footprint normalisation), per covered target pixel with output gradient g:
+//   dL/dS_k  += g w_k / F                                  (scatter, global atomics)
+//   dL/dx_s   = g / F * sum_k (dw_k/dx_s) (S_k - value)    (and likewise y)
+// and the source-WCS parameter gradients follow by the chain rule through the inverse SIP
+// (polynomial AP/BP, or the implicit-function derivative of the Newton inverse of A/B), CD^-1
+// and the gnomonic projection about (CRVAL1, CRVAL2). Per-pixel terms are FP32; each warp sums
+// them with shuffles and adds the warp total to an FP64 shared accumulator; each CTA writes
+// one FP64 partial per parameter and a final single-block kernel adds the partials in a fixed
+// order (deterministic parameter gradients).
+#include <climits>
+
 #include "dfr_device.cuh"
 
 namespace dfr {
+
+constexpr int kBwdThreads = 256;
+constexpr float kR0f = 57.29577951308232f;
+
+__host__ __device__ constexpr int nterms(int fd) { return fd > 0 ? (fd + 1) * (fd + 2) / 2 - 1 : 0; }
+
+// FP64 geometry of one target pixel: source position, intermediate offsets before (U, V) and
+// after (u, v) the inverse SIP. Same arithmetic as the forward FP64 path.
+__device__ __forceinline__ bool fp64_geo(const FwdPlan& P, double X, double Y, double& xs,
+                                         double& ys, double& U, double& V, double& u, double& v) {
+  if (P.identity) {
+    xs = X;
+    ys = Y;
+    U = u = X - P.crpix_s[0];
+    V = v = Y - P.crpix_s[1];
+    return true;
+  }
+  double ra, dec;
+  world_from_target_fp64(P, X, Y, ra, dec);
+  const bool ok = intermediate_from_world_fp64(P, ra, dec, U, V);
+  u = U;
+  v = V;
+  if (P.isip_deg > 0) {
+    double ga, gb;
+    horner_pair_rt<double>(P.isip_d[0], P.isip_d[1], P.isip_deg, U, V, ga, gb);
+    u = U + ga;
+    v = V + gb;
+  }
+  if ((P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0) newton_fp64(P, U, V, u, v);
+  xs = u + P.crpix_s[0];
+  ys = v + P.crpix_s[1];
+  return ok;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int ORDER, int FD>
+__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant__ FwdPlan P,
+                                                          const __grid_constant__ BwdExtra B) {
+  using T = Taps<ORDER>;
+  constexpr int NT = kBwdThreads, NW = NT / 32, PPT = kTilePix / NT;
+  constexpr int NTERM = nterms(FD);
+  constexpr int NP = 6 + 2 * NTERM;
+  __shared__ double sacc[NW][NP];
+  __shared__ Anchor sanc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < NW * NP; i += NT) sacc[i / NP][i % NP] = 0.0;
+  const bool split = (P.flags & DFR_SPLIT) != 0;
+  const bool exact = (P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0;
+  const bool want_params = B.grad_params != nullptr && ORDER != DFR_NEAREST;
+  const int ntiles = P.tiles_x * P.tiles_y;
+  // CD, CD^-1 and the tangent point in FP32 for the per-pixel chain rule
+  const float cd00 = float(P.cd_s[0][0]), cd01 = float(P.cd_s[0][1]);
+  const float cd10 = float(P.cd_s[1][0]), cd11 = float(P.cd_s[1][1]);
+  const float ci00 = float(P.cdinv_s[0][0]), ci01 = float(P.cdinv_s[0][1]);
+  const float ci10 = float(P.cdinv_s[1][0]), ci11 = float(P.cdinv_s[1][1]);
+  const float sd0 = float(P.sd0_s), cd0 = float(P.cd0_s);
+  __syncthreads();
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ox = (tile % P.tiles_x) * kTileW, oy = (tile / P.tiles_x) * kTileH;
+    const int ax = P.x0 + ox + kTileW / 2, ay = P.y0 + oy + kTileH / 2;
+    if (split) {
+      if (tid == 0) make_anchor(P, ax, ay, sanc);
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int k = 0; k < PPT; ++k) {
+      const int i = tid + k * NT;
+      const int gx = ox + (i % kTileW), gy = oy + (i / kTileW);
+      const bool inside = gx < P.w && gy < P.h;
+      bool cov = false;
+      int bx = 0, by = 0;
+      float xr = 0.f, yr = 0.f, U = 0.f, V = 0.f, u = 0.f, v = 0.f;
+      if (inside) {
+        if (split) {
+          const Anchor& a = sanc;
+          float geo[4];
+          const bool ok = split_coords<-1>(P, a, float(P.x0 + gx - ax), float(P.y0 + gy - ay),
+                                           xr, yr, geo);
+          bx = a.bx;
+          by = a.by;
+          cov = ok && xr >= -0.5f - float(bx) && xr <= float(P.W) - 0.5f - float(bx) &&
+                yr >= -0.5f - float(by) && yr <= float(P.H) - 0.5f - float(by);
+          U = a.U0 + geo[0];
+          V = a.V0 + geo[1];
+          u = a.U0 + geo[2];
+          v = a.V0 + geo[3];
+        } else {
+          double xs, ys, Ud, Vd, ud, vd;
+          const bool ok = fp64_geo(P, double(P.x0 + gx), double(P.y0 + gy), xs, ys, Ud, Vd, ud, vd);
+          const double rx = rint(xs), ry = rint(ys);
+          if (fabs(xs - rx) < kSnap) xs = rx;
+          if (fabs(ys - ry) < kSnap) ys = ry;
+          cov = ok && xs >= -0.5 && xs <= P.W - 0.5 && ys >= -0.5 && ys <= P.H - 0.5;
+          if (cov) {
+            const double fx = floor(xs), fy = floor(ys);
+            bx = int(fx);
+            by = int(fy);
+            xr = float(xs - fx);
+            yr = float(ys - fy);
+          }
+          U = float(Ud);
+          V = float(Vd);
+          u = float(ud);
+          v = float(vd);
+        }
+      }
+      float gxs = 0.f, gys = 0.f;  // dL/dx_s, dL/dy_s
+      if (cov) {
+        const float flx = floorf(xr), fly = floorf(yr);
+        const float tx = xr - flx, ty = yr - fly;
+        int ix = int(flx), iy = int(fly);
+        if (ORDER == DFR_NEAREST) {
+          ix += tx >= 0.5f;
+          iy += ty >= 0.5f;
+        }
+        ix += bx + T::lo;
+        iy += by + T::lo;
+        float wx[T::n], wy[T::n], dx[T::n], dy[T::n], s[T::n][T::n];
+        weights<ORDER, float>(tx, wx);
+        weights<ORDER, float>(ty, wy);
+        dweights<ORDER, float>(tx, dx);
+        dweights<ORDER, float>(ty, dy);
+        float sx = 0.f, sy = 0.f;
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) {
+          const bool inx = unsigned(ix + q) < unsigned(P.W);
+          const bool iny = unsigned(iy + q) < unsigned(P.H);
+          wx[q] = inx ? wx[q] : 0.f;
+          dx[q] = inx ? dx[q] : 0.f;
+          wy[q] = iny ? wy[q] : 0.f;
+          dy[q] = iny ? dy[q] : 0.f;
+          sx += wx[q];
+          sy += wy[q];
+        }
+        float num = 0.f;
+#pragma unroll
+        for (int r = 0; r < T::n; ++r) {
+          const bool iny = unsigned(iy + r) < unsigned(P.H);
+          float row = 0.f;
+#pragma unroll
+          for (int q = 0; q < T::n; ++q) {
+            const bool in = iny && unsigned(ix + q) < unsigned(P.W);
+            s[r][q] = in ? __ldg(P.img + int64_t(iy + r) * P.pitch + (ix + q)) : 0.f;
+            row = fmaf(wx[q], s[r][q], row);
+          }
+          num = fmaf(wy[r], row, num);
+        }
+        const float F = sx * sy;
+        if (F != 0.f) {
+          const float g = B.grad_out[int64_t(gy) * B.go_pitch + gx];
+          const float gF = __fdividef(g, F);
+          if (B.grad_src) {
+#pragma unroll
+            for (int r = 0; r < T::n; ++r)
+#pragma unroll
+              for (int q = 0; q < T::n; ++q) {
+                const float w = wx[q] * wy[r];
+                if (w != 0.f)
+                  atomicAdd(B.grad_src + int64_t(iy + r) * B.gs_pitch + (ix + q), gF * w);
+              }
+          }
+          if (want_params) {
+            const float val = __fdividef(num, F);
+            float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+            for (int r = 0; r < T::n; ++r)
+#pragma unroll
+              for (int q = 0; q < T::n; ++q) {
+                const float d = s[r][q] - val;
+                ax_ = fmaf(dx[q] * wy[r], d, ax_);
+                ay_ = fmaf(wx[q] * dy[r], d, ay_);
+              }
+            gxs = gF * ax_;
+            gys = gF * ay_;
+          }
+        }
+      }
+      if (!want_params) continue;  // uniform over the launch
+      // chain rule: (gxs, gys) -> lambda = dL/d(U, V)
+      float m00 = 1.f, m01 = 0.f, m10 = 0.f, m11 = 1.f;
+      if (cov) {
+        if (exact) {
+          float A, Au, Av, Bq, Bu, Bv;
+          horner_grad_rt<float>(P.fsip_f[0], P.fsip_deg, u, v, A, Au, Av);
+          horner_grad_rt<float>(P.fsip_f[1], P.fsip_deg, u, v, Bq, Bu, Bv);
+          const float j00 = 1.f + Au, j01 = Av, j10 = Bu, j11 = 1.f + Bv;
+          const float inv = __fdividef(1.f, fmaf(j00, j11, -j01 * j10));
+          m00 = j11 * inv;
+          m01 = -j01 * inv;
+          m10 = -j10 * inv;
+          m11 = j00 * inv;
+        } else if (P.isip_deg > 0) {
+          float A, Au, Av, Bq, Bu, Bv;
+          horner_grad_rt<float>(P.isip_f[0], P.isip_deg, U, V, A, Au, Av);
+          horner_grad_rt<float>(P.isip_f[1], P.isip_deg, U, V, Bq, Bu, Bv);
+          m00 = 1.f + Au;
+          m01 = Av;
+          m10 = Bu;
+          m11 = 1.f + Bv;
+        }
+      }
+      const float lu = fmaf(gxs, m00, gys * m10);
+      const float lv = fmaf(gxs, m01, gys * m11);
+      // nu = CD^-T lambda = dL/d(u', v') (degrees)
+      const float nx = fmaf(ci00, lu, ci10 * lv);
+      const float ny = fmaf(ci01, lu, ci11 * lv);
+      const float xi = fmaf(cd00, U, cd01 * V) / kR0f;
+      const float eta = fmaf(cd10, U, cd11 * V) / kR0f;
+      float c[6];
+      c[0] = nx * fmaf(-cd0, fmaf(xi, xi, 1.f), sd0 * eta) + ny * (-xi * fmaf(cd0, eta, sd0));
+      c[1] = nx * (-xi * eta) + ny * (-fmaf(eta, eta, 1.f));
+      c[2] = -nx * U;
+      c[3] = -nx * V;
+      c[4] = -ny * U;
+      c[5] = -ny * V;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float t = warp_sum(c[q]);
+        if (lane == 0) sacc[warp][q] += double(t);
+      }
+      if (FD > 0) {
+        float up[FD + 1], vp[FD + 1];
+        up[0] = vp[0] = 1.f;
+#pragma unroll
+        for (int e = 1; e <= FD; ++e) {
+          up[e] = up[e - 1] * u;
+          vp[e] = vp[e - 1] * v;
+        }
+        int t = 0;
+#pragma unroll
+        for (int n = 1; n <= FD; ++n)
+#pragma unroll
+          for (int p = n; p >= 0; --p, ++t) {
+            const float m = up[p] * vp[n - p];
+            const float ta = warp_sum(-lu * m);
+            const float tb = warp_sum(-lv * m);
+            if (lane == 0) {
+              sacc[warp][6 + t] += double(ta);
+              sacc[warp][6 + NTERM + t] += double(tb);
+            }
+          }
+      }
+    }
+    __syncthreads();  // the shared anchor is rewritten by the next tile
+  }
+  if (B.partials) {
+    for (int q = tid; q < NP; q += NT) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += sacc[w][q];
+      B.partials[int64_t(blockIdx.x) * NP + q] = s;
+    }
+  }
+}
+
+// Sum the per-CTA partials in a fixed order and scatter them to the public layout.
+__global__ void bwd_finalize(const __grid_constant__ BwdExtra B, int np) {
+  for (int j = threadIdx.x; j < B.nout; j += blockDim.x) B.grad_params[j] = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    const int dst = B.pmap[q];
+    if (dst < 0) continue;
+    double s = 0.0;
+    for (int b = 0; b < B.grid; ++b) s += B.partials[int64_t(b) * np + q];
+    B.grad_params[dst] = s;
+  }
+}
+
+int backward_num_padded(int fd) { return 6 + 2 * nterms(fd); }
+int backward_threads() { return kBwdThreads; }
+
+template <int ORDER>
+static const void* bwd_for_order(int fd) {
+  switch (fd) {
+    case 0: return reinterpret_cast<const void*>(&bwd_kernel<ORDER, 0>);
+    case 3: return reinterpret_cast<const void*>(&bwd_kernel<ORDER, 3>);
+    case 5: return reinterpret_cast<const void*>(&bwd_kernel<ORDER, 5>);
+    default: return reinterpret_cast<const void*>(&bwd_kernel<ORDER, 9>);
+  }
+}
+
+static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
+  switch (p0.order) {
+    case DFR_NEAREST: return bwd_for_order<DFR_NEAREST>(fd);
+    case DFR_BILINEAR: return bwd_for_order<DFR_BILINEAR>(fd);
+    default: return bwd_for_order<DFR_BICUBIC>(fd);
+  }
+}
+
+int backward_max_blocks_per_sm(const FwdPlan& p0, int fd) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwd_kernel_for(p0, fd), kBwdThreads,
+                                                    0) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s) {
+  FwdPlan p = p0;
+  BwdExtra b = B;
+  void* args[] = {&p, &b};
+  cudaError_t e = cudaLaunchKernel(bwd_kernel_for(p0, B.fd), dim3(B.grid), dim3(kBwdThreads),
+                                   args, 0, s);
+  if (e != cudaSuccess || B.grad_params == nullptr) return e;
+  int np = backward_num_padded(B.fd);
+  void* fargs[] = {&b, &np};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(&bwd_finalize), dim3(1), dim3(128),
+                          fargs, 0, s);
+}
 
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s) {
   int32_t zero = 0;

@@ -243,7 +243,9 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
     a.bx = ax;
     a.by = ay;
     a.f0x = a.f0y = 0.f;
-    a.U0 = a.V0 = 0.f;
+    // true intermediate offsets of the anchor (used only by the adjoint's chain rule)
+    a.U0 = float(double(ax) - P.crpix_s[0]);
+    a.V0 = float(double(ay) - P.crpix_s[1]);
     a.a0 = 1.f; a.a1 = 0.f; a.b0 = 0.f; a.b1 = 1.f;
     a.g20 = a.g21 = 0.f;
     a.h2 = 1.f;
@@ -291,12 +293,19 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
 
 // FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor pixel.
 // Writes the source position relative to (bx, by); returns false if undefined.
+// IDEG > 0: unrolled inverse-SIP Horner of that degree; IDEG < 0: runtime degree; 0: none.
+// geo (nullable) receives (du, dv, eu, ev) for the adjoint.
 template <int IDEG>
 __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, float dx,
-                                             float dy, float& xr, float& yr) {
+                                             float dy, float& xr, float& yr,
+                                             float* geo = nullptr) {
   if (P.identity) {
     xr = dx;
     yr = dy;
+    if (geo) {
+      geo[0] = geo[2] = dx;
+      geo[1] = geo[3] = dy;
+    }
     return true;
   }
   float dp = dx, dq = dy;
@@ -314,7 +323,14 @@ __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, 
   float eu = du, ev = dv;
   if (IDEG > 0) {
     float ga, gb;
-    horner_pair<IDEG, float>(P.isip_f[0], P.isip_f[1], a.U0 + du, a.V0 + dv, ga, gb);
+    horner_pair<(IDEG > 0 ? IDEG : 1), float>(P.isip_f[0], P.isip_f[1], a.U0 + du, a.V0 + dv,
+                                              ga, gb);
+    eu = du + ga;
+    ev = dv + gb;
+  } else if (IDEG < 0 && P.isip_deg > 0) {
+    // runtime degree: the same FMA sequence as the unrolled form, so the same bits
+    float ga, gb;
+    horner_pair_rt<float>(P.isip_f[0], P.isip_f[1], P.isip_deg, a.U0 + du, a.V0 + dv, ga, gb);
     eu = du + ga;
     ev = dv + gb;
   }
@@ -334,6 +350,12 @@ __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, 
   }
   xr = a.f0x + eu;
   yr = a.f0y + ev;
+  if (geo) {
+    geo[0] = du;  // source intermediate offsets before the inverse SIP, relative to (U0, V0)
+    geo[1] = dv;
+    geo[2] = eu;  // ... and after it
+    geo[3] = ev;
+  }
   return den > 0.f && a.h2 > 0.f;
 }
 

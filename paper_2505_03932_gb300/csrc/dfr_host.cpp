@@ -373,6 +373,7 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   P.sd0_s = std::sin(src->crval[1] * kDeg);
   P.cd0_s = std::cos(src->crval[1] * kDeg);
   cd_inverse(src->cd, P.cdinv_s);
+  std::memcpy(P.cd_s, src->cd, sizeof(P.cd_s));
 
   // Split path: TAN -> sky -> TAN is projective. With F = tangent frame (east, north, centre),
   // a target standard coordinate (xi, eta) maps to F_s^T F_t (xi, eta, 1) in the source frame.
@@ -406,10 +407,18 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
       G[i][j] = s;
     }
   const double g22 = G[2][2];
-  if (!(g22 > 0.0))
-    return fail(DFR_ERR_UNSUPPORTED_WCS, "target and source tangent points are >= 90 deg apart");
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) P.G[i][j] = G[i][j] / g22;
+  if (!(g22 > 0.0)) {
+    // the projective form needs the two tangent points less than 90 deg apart; the all-FP64
+    // path evaluates the spherical formulas per pixel and has no such limit
+    if (flags & DFR_SPLIT)
+      return fail(DFR_ERR_UNSUPPORTED_WCS,
+                  "split precision needs tangent points < 90 deg apart; use DFR_FP64");
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) P.G[i][j] = G[i][j];
+  } else {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) P.G[i][j] = G[i][j] / g22;
+  }
 
   // TMA staging of the source tile (split path only)
   P.use_tma = 0;
@@ -953,14 +962,99 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   return DFR_OK;
 }
 
+namespace dfr {
+namespace {
+
+// Per-device scratch for the adjoint's per-CTA parameter partials (grown on demand).
+struct BwdScratch {
+  double* partials = nullptr;
+  size_t cap = 0;  // doubles
+  int sms = 0;
+};
+std::map<int, BwdScratch> g_bwd;
+
+int padded_fd(int order) {
+  if (order <= 0) return 0;
+  if (order <= 3) return 3;
+  if (order <= 5) return 5;
+  return 9;
+}
+
+}  // namespace
+}  // namespace dfr
+
 extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       const float* src_img, int64_t src_pitch,
                                       const float* grad_out, int64_t go_pitch, int32_t x0,
                                       int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
                                       uint32_t flags, float* grad_src, int64_t gs_pitch,
                                       double* grad_params, void* stream) {
-  (void)src; (void)tgt; (void)src_img; (void)src_pitch; (void)grad_out; (void)go_pitch;
-  (void)x0; (void)y0; (void)out_w; (void)out_h; (void)order; (void)flags; (void)grad_src;
-  (void)gs_pitch; (void)grad_params; (void)stream;
-  return fail(DFR_ERR_INVALID_ARG, "backward not built yet");
+  FwdPlan P;
+  // the forward plan (outputs unused) gives the same source positions as dfr_reproject
+  float* dummy = reinterpret_cast<float*>(uintptr_t(16));
+  int rc = build_plan(src, tgt, src_img, src_pitch, dummy, nullptr, out_w, x0, y0, out_w, out_h,
+                      order, flags | DFR_NO_TMA, nullptr, -1, P);
+  if (rc != DFR_OK) return rc;
+  if (out_w > 0 && out_h > 0) {
+    if (!grad_out) return fail(DFR_ERR_INVALID_ARG, "grad_out must be non-NULL");
+    if (go_pitch < out_w) return fail(DFR_ERR_INVALID_ARG, "grad_out pitch < width");
+    if (grad_src && gs_pitch < src->naxis[0])
+      return fail(DFR_ERR_INVALID_ARG, "grad_src pitch < NAXIS1");
+  }
+  P.out = nullptr;
+  BwdExtra B;
+  std::memset(&B, 0, sizeof(B));
+  B.grad_src = grad_src;
+  B.gs_pitch = gs_pitch;
+  B.grad_out = grad_out;
+  B.go_pitch = go_pitch;
+  B.grad_params = grad_params;
+  B.nout = dfr_num_params(src);
+  const bool exact = (flags & DFR_EXACT_INVERSE) && (src->a_order > 0 || src->b_order > 0);
+  B.fd = exact ? padded_fd(std::max(src->a_order, src->b_order)) : 0;
+  // padded layout -> public layout
+  const int np = backward_num_padded(B.fd);
+  for (int k = 0; k < kMaxParams; ++k) B.pmap[k] = -1;
+  for (int k = 0; k < 6; ++k) B.pmap[k] = int16_t(k);
+  if (B.fd > 0) {
+    const int nt = (np - 6) / 2;
+    int t = 0, ia = 6;
+    const int ntA = src->a_order > 0 ? (src->a_order + 1) * (src->a_order + 2) / 2 - 1 : 0;
+    int ib = 6 + ntA;
+    for (int n = 1; n <= B.fd; ++n)
+      for (int p = n; p >= 0; --p, ++t) {
+        if (n <= src->a_order) B.pmap[6 + t] = int16_t(ia++);
+        if (n <= src->b_order) B.pmap[6 + nt + t] = int16_t(ib++);
+      }
+  }
+  if (out_w == 0 || out_h == 0 || (!grad_src && !grad_params)) {
+    if (grad_params) {
+      cudaError_t e = cudaMemsetAsync(grad_params, 0, sizeof(double) * size_t(B.nout),
+                                      static_cast<cudaStream_t>(stream));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    return DFR_OK;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  DFR_CUDA(cudaGetDevice(&dev));
+  BwdScratch& S = g_bwd[dev];
+  if (S.sms == 0) DFR_CUDA(cudaDeviceGetAttribute(&S.sms, cudaDevAttrMultiProcessorCount, dev));
+  const int ntiles = P.tiles_x * P.tiles_y;
+  const int per_sm = std::min(4, backward_max_blocks_per_sm(P, B.fd));
+  B.grid = std::max(1, std::min(ntiles, S.sms * per_sm));
+  if (grad_params) {
+    const size_t need = size_t(B.grid) * size_t(np);
+    if (need > S.cap) {
+      if (S.partials) cudaFree(S.partials);
+      S.partials = nullptr;
+      S.cap = 0;
+      DFR_CUDA(cudaMalloc(&S.partials, need * sizeof(double)));
+      S.cap = need;
+    }
+    B.partials = S.partials;
+  }
+  cudaError_t e = launch_backward(P, B, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject_backward launch");
+  return DFR_OK;
 }

@@ -63,6 +63,7 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   double cd_t[2][2];
   double ra0_s, sd0_s, cd0_s;
   double cdinv_s[2][2];
+  double cd_s[2][2];
   int32_t flags;
   int32_t order;
 };
@@ -78,17 +79,21 @@ struct FwdLaunch {
   int32_t smem_box_floats;   // dynamic shared memory reserved for the source box
 };
 
-// Backward plan extras (parameter layout of dfr_reproject_backward).
+// Backward launch arguments. The kernel accumulates parameter gradients in a padded layout
+// (6 + 2 * terms(fd)); pmap sends each padded entry to its dfr_reproject_backward index (-1:
+// not a parameter of this WCS).
+constexpr int kMaxParams = 6 + 2 * (kMaxCoef - 1);  // 114
 struct BwdExtra {
-  float* grad_src;
+  float* grad_src;           // nullable
   int64_t gs_pitch;
   const float* grad_out;
   int64_t go_pitch;
-  double* grad_params;       // final (nparams)
-  double* partials;          // scratch: nblocks x nparams
-  int32_t nparams;
-  int32_t na, nb;            // number of A and B terms
-  int32_t a_deg, b_deg;      // source A/B orders (for the parameter monomials)
+  double* grad_params;       // nullable: final, nout entries
+  double* partials;          // scratch: grid x np per-block sums
+  int32_t nout;              // dfr_num_params(src)
+  int32_t fd;                // padded A/B degree of the parameter layout (0: A/B not live)
+  int32_t grid;
+  int16_t pmap[kMaxParams];
 };
 
 // Device status word: bit 0 = a bounded wait timed out, bit 1 = internal check failed.
@@ -103,5 +108,8 @@ int forward_threads_default();
 cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
+int backward_num_padded(int fd);
+int backward_max_blocks_per_sm(const FwdPlan& p0, int fd);
+int backward_threads();
 
 }  // namespace dfr

@@ -169,19 +169,24 @@ def test_far_tangent_points_and_target_sip():
 
 
 def test_source_far_hemisphere_is_uncovered():
-    """A target grid spanning >90 deg: pixels whose sky position is on the far side of the source
-    projection are uncovered. The FP64 path decides per pixel exactly like the oracle; the split
-    path (FP64 anchor per 64x16 tile) never covers such a pixel."""
+    """A wide target grid whose tangent point is 80 deg from the source's: pixels whose sky
+    position lies on the far hemisphere of the source projection are uncovered. The FP64 path
+    decides per pixel exactly like the oracle; the split path (FP64 anchor per tile) never
+    covers such a pixel."""
     src = synth.tan_wcs(64, 64, crval=(0.0, 0.0))
-    tgt = synth.tan_wcs(64, 64, crval=(0.0, 0.0), scale_arcsec=3600.0 * 4)  # 4 deg/px
+    tgt = synth.tan_wcs(64, 64, crval=(80.0, 0.0), scale_arcsec=3600.0 * 3)  # 3 deg/px
     img = np.ones((64, 64), np.float32)
     X, Y = np.meshgrid(np.arange(64.0), np.arange(64.0))
     _, _, ok = OR.coords(src, tgt, X, Y)
-    assert (~ok).any()
+    assert (~ok).any() and ok.any()
     val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", "fp64", (0, 0, 64, 64))
     assert np.array_equal(np.isfinite(cr[..., 0]), ok)
     val, fp, cr = gpu(src, tgt, to_dev(img), "bilinear", "split", (0, 0, 64, 64))
     assert np.all(fp[~ok] == 0) and np.all(val[~ok] == 0)
+    far = synth.tan_wcs(64, 64, crval=(120.0, 0.0))
+    with pytest.raises(dfr().DfrError):
+        dfr().reproject(to_dev(img), src, far, order="bilinear", precision="split")
+    dfr().reproject(to_dev(img), src, far, order="bilinear", precision="fp64")
 
 
 def test_config1_full_size_sampled():
