@@ -82,51 +82,43 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
   }
 }
 
-// ------------------------------------------------------------------ split-precision tile
-struct TileShared {
-  Anchor anc;
-  int32_t red[5];  // min fx, max fx, min fy, max fy, any covered
+// ------------------------------------------------------------------ split-precision tiles
+// One warp owns a 32x8 tile: lane = column, 8 rows per lane. Per tile: source positions of the
+// 256 pixels (FP32, from the tile's FP64 anchor), warp min/max of their integer parts, one TMA
+// load of the covering source box into the warp's shared buffer, then the gather. Tiles are
+// double-buffered: the box of tile t+1 is in flight while tile t is gathered.
+struct TileCoords {
+  float x[kTileH], y[kTileH];  // source position relative to (bx, by)
+  uint32_t mask;               // covered rows of this lane
+  int32_t bx, by;              // anchor base
+  int32_t bx0, by0;            // box origin (absolute source pixel)
+  bool use_box;
 };
 
-template <int ORDER, int IDEG, int NT>
-__device__ __forceinline__ void split_tile(const FwdPlan& P, int tile, float* box, uint64_t* bar,
-                                           uint32_t& phase, TileShared& sh) {
+template <int ORDER, int IDEG>
+__device__ __forceinline__ void split_prepare(const FwdPlan& P, const Anchor& a, int local,
+                                              int lane, float* box, uint64_t* bar,
+                                              TileCoords& C) {
   using T = Taps<ORDER>;
-  constexpr int PPT = kTilePix / NT;
-  const int tid = threadIdx.x;
-  const int ox = (tile % P.tiles_x) * kTileW, oy = (tile / P.tiles_x) * kTileH;
-  const int ax = P.x0 + ox + kTileW / 2, ay = P.y0 + oy + kTileH / 2;
-
-  if (tid == 0) {
-    make_anchor(P, ax, ay, sh.anc);
-    sh.red[0] = INT_MAX;
-    sh.red[1] = INT_MIN;
-    sh.red[2] = INT_MAX;
-    sh.red[3] = INT_MIN;
-    sh.red[4] = 0;
-  }
-  __syncthreads();
-  const Anchor a = sh.anc;
-
-  float xr[PPT], yr[PPT];
-  uint32_t covmask = 0;
-  int mnx = INT_MAX, mxx = INT_MIN, mny = INT_MAX, mxy = INT_MIN;
+  const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
+  const int gx = ox + lane;
   const float xlo = -0.5f - float(a.bx), xhi = float(P.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(P.H) - 0.5f - float(a.by);
+  int mnx = INT_MAX, mxx = INT_MIN, mny = INT_MAX, mxy = INT_MIN;
+  C.mask = 0;
+  C.bx = a.bx;
+  C.by = a.by;
+  const float dx = float(P.x0 + gx - a.ax);
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int i = tid + k * NT;
-    const int lx = i % kTileW, ly = i / kTileW;
-    const int gx = ox + lx, gy = oy + ly;
+  for (int r = 0; r < kTileH; ++r) {
+    const int gy = oy + r;
     const bool inside = gx < P.w && gy < P.h;
     float x, y;
-    const bool ok = split_coords<IDEG>(P, a, float(ox + lx + P.x0 - ax), float(oy + ly + P.y0 - ay),
-                                       x, y);
-    xr[k] = x;
-    yr[k] = y;
-    const bool cov = inside && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi;
-    if (cov) {
-      covmask |= 1u << k;
+    const bool ok = split_coords<IDEG>(P, a, dx, float(P.y0 + gy - a.ay), x, y);
+    C.x[r] = x;
+    C.y[r] = y;
+    if (inside && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
+      C.mask |= 1u << r;
       const int fx = int(floorf(x)), fy = int(floorf(y));
       mnx = min(mnx, fx);
       mxx = max(mxx, fx);
@@ -139,52 +131,52 @@ __device__ __forceinline__ void split_tile(const FwdPlan& P, int tile, float* bo
       c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
     }
   }
-  // coverage and source-extent reduction: warp shuffles, then one shared atomic per warp
-  const unsigned any = __ballot_sync(0xffffffffu, covmask != 0);
-  if (any) {
+  // coverage and source extent of the tile: warp-level reductions
+  const bool any = __ballot_sync(0xffffffffu, C.mask != 0) != 0;
+  C.use_box = false;
+  C.bx0 = C.by0 = 0;
+  if (any && P.use_tma) {
     mnx = __reduce_min_sync(0xffffffffu, mnx);
     mxx = __reduce_max_sync(0xffffffffu, mxx);
     mny = __reduce_min_sync(0xffffffffu, mny);
     mxy = __reduce_max_sync(0xffffffffu, mxy);
-    if ((tid & 31) == 0) {
-      atomicMin(&sh.red[0], mnx);
-      atomicMax(&sh.red[1], mxx);
-      atomicMin(&sh.red[2], mny);
-      atomicMax(&sh.red[3], mxy);
-      atomicOr(&sh.red[4], 1);
-    }
-  }
-  __syncthreads();
-  const bool tile_any = sh.red[4] != 0;
-  int bx0 = 0, by0 = 0;
-  bool use_box = false;
-  if (tile_any && P.use_tma) {
-    bx0 = (a.bx + sh.red[0] + T::lo) & ~3;  // TMA x must be a multiple of 16 bytes
-    by0 = a.by + sh.red[2] + T::lo;
+    C.bx0 = (a.bx + mnx + T::lo) & ~3;  // TMA x must be a multiple of 16 bytes
+    C.by0 = a.by + mny + T::lo;
     // nearest may step one pixel up from floor(x), so its extent is two taps wide
     constexpr int ext = (ORDER == DFR_NEAREST) ? 2 : T::n;
-    const int need_w = a.bx + sh.red[1] + T::lo + ext - bx0;
-    const int need_h = a.by + sh.red[3] + T::lo + ext - by0;
-    use_box = need_w <= P.box_w && need_h <= P.box_h;
+    C.use_box = (a.bx + mxx + T::lo + ext - C.bx0 <= P.box_w) &&
+                (a.by + mxy + T::lo + ext - C.by0 <= P.box_h);
   }
-  if (use_box) {
-    if (tid == 0) {
+  if (C.use_box) {
+    __syncwarp();  // every lane is done reading this buffer's previous tile
+    if (lane == 0) {
       fence_proxy_async();
       mbar_expect_tx(bar, uint32_t(P.box_w) * uint32_t(P.box_h) * 4u);
-      tma_load_2d(box, &P.tmap, bar, bx0, by0);
+      tma_load_2d(box, &P.tmap, bar, C.bx0, C.by0);
     }
+  }
+}
+
+template <int ORDER>
+__device__ __forceinline__ void split_consume(const FwdPlan& P, int local, int lane,
+                                              const float* box, uint64_t* bar, uint32_t& phase,
+                                              const TileCoords& C) {
+  using T = Taps<ORDER>;
+  const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
+  const int gx = ox + lane;
+  bool use_box = C.use_box;
+  if (use_box) {
     if (!mbar_wait(bar, phase)) use_box = false;  // timed out: gather from global instead
     phase ^= 1u;
   }
-
+  if (gx >= P.w) return;
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int i = tid + k * NT;
-    const int gx = ox + (i % kTileW), gy = oy + (i / kTileW);
-    if (gx >= P.w || gy >= P.h) continue;
+  for (int r = 0; r < kTileH; ++r) {
+    const int gy = oy + r;
+    if (gy >= P.h) break;
     float val = 0.f, fpv = 0.f;
-    if (covmask & (1u << k)) {
-      const float x = xr[k], y = yr[k];
+    if (C.mask & (1u << r)) {
+      const float x = C.x[r], y = C.y[r];
       const float flx = floorf(x), fly = floorf(y);
       const float tx = x - flx, ty = y - fly;
       int ix = int(flx), iy = int(fly);
@@ -192,8 +184,8 @@ __device__ __forceinline__ void split_tile(const FwdPlan& P, int tile, float* bo
         ix += tx >= 0.5f;
         iy += ty >= 0.5f;
       }
-      ix += a.bx + T::lo;  // absolute source column of the first tap
-      iy += a.by + T::lo;
+      ix += C.bx + T::lo;  // absolute source column / row of the first tap
+      iy += C.by + T::lo;
       float wx[T::n], wy[T::n];
       weights<ORDER, float>(tx, wx);
       weights<ORDER, float>(ty, wy);
@@ -207,26 +199,26 @@ __device__ __forceinline__ void split_tile(const FwdPlan& P, int tile, float* bo
       }
       float num = 0.f;
       if (use_box) {
-        const float* b = box + (iy - by0) * P.box_w + (ix - bx0);
+        const float* b = box + (iy - C.by0) * P.box_w + (ix - C.bx0);
 #pragma unroll
-        for (int r = 0; r < T::n; ++r) {
+        for (int k = 0; k < T::n; ++k) {
           float row = 0.f;
 #pragma unroll
-          for (int q = 0; q < T::n; ++q) row = fmaf(wx[q], b[r * P.box_w + q], row);
-          num = fmaf(wy[r], row, num);
+          for (int q = 0; q < T::n; ++q) row = fmaf(wx[q], b[k * P.box_w + q], row);
+          num = fmaf(wy[k], row, num);
         }
       } else {
 #pragma unroll
-        for (int r = 0; r < T::n; ++r) {
+        for (int k = 0; k < T::n; ++k) {
           float row = 0.f;
-          const bool iny = unsigned(iy + r) < unsigned(P.H);
+          const bool iny = unsigned(iy + k) < unsigned(P.H);
 #pragma unroll
           for (int q = 0; q < T::n; ++q) {
             const bool in = iny && unsigned(ix + q) < unsigned(P.W);
-            const float s = in ? __ldg(P.img + int64_t(iy + r) * P.pitch + (ix + q)) : 0.f;
+            const float s = in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q)) : 0.f;
             row = fmaf(wx[q], s, row);
           }
-          num = fmaf(wy[r], row, num);
+          num = fmaf(wy[k], row, num);
         }
       }
       const float f = sx * sy;
@@ -239,7 +231,6 @@ __device__ __forceinline__ void split_tile(const FwdPlan& P, int tile, float* bo
     __stcs(P.out + o, val);
     if (P.fp) __stcs(P.fp + o, fpv);
   }
-  __syncthreads();  // the box and the shared anchor are reused by the next tile
 }
 
 // ------------------------------------------------------------------ kernels
@@ -266,35 +257,93 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
   }
 }
 
-template <int ORDER, int IDEG, int NT>
-__global__ void __launch_bounds__(NT) fwd_split_kernel(const __grid_constant__ FwdPlan p0,
-                                                       const FwdLaunch L) {
-  extern __shared__ __align__(128) float box_raw[];
-  // TMA destinations are kept 128-byte aligned (the launch reserves 128 bytes of slack)
-  float* box = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(box_raw) + 127) &
-                                        ~uintptr_t(127));
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ TileShared sh;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  uint32_t phase = 0;
-  if (L.plans == nullptr) {
-    split_tile<ORDER, IDEG, NT>(p0, blockIdx.x, box, &bar, phase, sh);
-    return;
+__device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
+  int lo = 0, hi = L.nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
-  __shared__ int32_t s_tile;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(L.counter, 1);
-    __syncthreads();
-    const int t = s_tile;
-    __syncthreads();
-    if (t >= L.tile_start[L.nframes]) break;
-    int lo = 0, hi = L.nframes - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  return lo;
+}
+
+template <int ORDER, int IDEG>
+__global__ void __launch_bounds__(kWarps * 32) fwd_split_kernel(const __grid_constant__ FwdPlan p0,
+                                                                const FwdLaunch L) {
+  extern __shared__ __align__(128) float box_raw[];
+  __shared__ Anchor s_anc[kWarps][kChunk];
+  __shared__ int32_t s_frame[kWarps][kChunk];
+  __shared__ int32_t s_local[kWarps][kChunk];
+  __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // two 128-byte aligned source-box buffers per warp (the launch reserves 128 bytes of slack)
+  float* box0 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(box_raw) + 127) &
+                                         ~uintptr_t(127)) + warp * 2 * L.box_floats;
+  float* box1 = box0 + L.box_floats;
+  uint64_t* bar0 = &s_bar[warp][0];
+  uint64_t* bar1 = &s_bar[warp][1];
+  if (lane == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+  }
+  __syncwarp();
+  uint32_t ph0 = 0, ph1 = 0;
+  const bool batch = L.plans != nullptr;
+  const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
+  const int nchunks = (total + kChunk - 1) / kChunk;
+  const int stride = gridDim.x * kWarps;
+  int chunk = blockIdx.x * kWarps + warp;
+  if (batch) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(L.counter, 1);
+    chunk = __shfl_sync(0xffffffffu, c, 0);
+  }
+  while (chunk < nchunks) {
+    const int t0 = chunk * kChunk;
+    const int nt = min(kChunk, total - t0);
+    if (lane < nt) {  // FP64 anchors of the chunk's tiles, one per lane
+      int f = 0, local = t0 + lane;
+      if (batch) {
+        f = frame_of(L, local);
+        local -= L.tile_start[f];
+      }
+      const FwdPlan& P = batch ? L.plans[f] : p0;
+      const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
+      make_anchor(P, P.x0 + ox + kTileW / 2, P.y0 + oy + kTileH / 2, s_anc[warp][lane]);
+      s_frame[warp][lane] = f;
+      s_local[warp][lane] = local;
     }
-    split_tile<ORDER, IDEG, NT>(L.plans[lo], t - L.tile_start[lo], box, &bar, phase, sh);
+    __syncwarp();
+    TileCoords CA, CB;
+    {
+      const FwdPlan& P = batch ? L.plans[s_frame[warp][0]] : p0;
+      split_prepare<ORDER, IDEG>(P, s_anc[warp][0], s_local[warp][0], lane, box0, bar0, CA);
+    }
+    for (int t = 0; t < nt; t += 2) {
+      const FwdPlan& Pa = batch ? L.plans[s_frame[warp][t]] : p0;
+      if (t + 1 < nt) {
+        const FwdPlan& Pb = batch ? L.plans[s_frame[warp][t + 1]] : p0;
+        split_prepare<ORDER, IDEG>(Pb, s_anc[warp][t + 1], s_local[warp][t + 1], lane, box1, bar1,
+                                   CB);
+      }
+      split_consume<ORDER>(Pa, s_local[warp][t], lane, box0, bar0, ph0, CA);
+      if (t + 1 < nt) {
+        if (t + 2 < nt) {
+          const FwdPlan& Pc = batch ? L.plans[s_frame[warp][t + 2]] : p0;
+          split_prepare<ORDER, IDEG>(Pc, s_anc[warp][t + 2], s_local[warp][t + 2], lane, box0,
+                                     bar0, CA);
+        }
+        const FwdPlan& Pb = batch ? L.plans[s_frame[warp][t + 1]] : p0;
+        split_consume<ORDER>(Pb, s_local[warp][t + 1], lane, box1, bar1, ph1, CB);
+      }
+    }
+    __syncwarp();  // anchors of this chunk are no longer read
+    if (batch) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(L.counter, 1);
+      chunk = __shfl_sync(0xffffffffu, c, 0);
+    } else {
+      chunk += stride;
+    }
   }
 }
 
@@ -306,10 +355,10 @@ template <int ORDER>
 static const void* kernel_for_order(bool split, int ideg) {
   if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kThreads>);
   switch (ideg) {
-    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0, kThreads>);
-    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4, kThreads>);
-    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6, kThreads>);
-    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9, kThreads>);
+    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0>);
+    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4>);
+    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6>);
+    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9>);
   }
 }
 

@@ -294,6 +294,8 @@ void size_box(FwdPlan& P) {
   P.box_h = bh;
 }
 
+int smem_for_floats(int floats);
+
 int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
                float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
                int32_t h, int32_t order, uint32_t flags, double* coords, int ideg_override,
@@ -425,7 +427,8 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   if ((flags & DFR_SPLIT) && !(flags & DFR_NO_TMA) && w > 0 && h > 0) {
     size_box(P);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
-    const bool fits = P.box_w <= 256 && P.box_h <= 256 && P.box_w * P.box_h * 4 <= 64 * 1024;
+    const int floats = (P.box_w * P.box_h + 31) & ~31;
+    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 112 * 1024;
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (aligned && fits && enc) {
       cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
@@ -442,8 +445,12 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   return DFR_OK;
 }
 
-// Dynamic shared memory of a split launch: the source box plus 128 bytes of alignment slack.
-int smem_for(const FwdPlan& P) { return P.use_tma ? P.box_w * P.box_h * 4 + 128 : 0; }
+// Floats of one source-box buffer (a multiple of 32, so every buffer stays 128-byte aligned).
+int box_floats(const FwdPlan& P) { return P.use_tma ? ((P.box_w * P.box_h + 31) & ~31) : 0; }
+
+// Dynamic shared memory of a split launch: two box buffers per warp plus 128 bytes of slack.
+int smem_for_floats(int floats) { return floats ? kWarps * 2 * floats * 4 + 128 : 0; }
+int smem_for(const FwdPlan& P) { return smem_for_floats(box_floats(P)); }
 
 // ------------------------------------------------------------------------------ device ctx
 // Library-owned device memory and graphs for the batched path, per device.
@@ -794,7 +801,22 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
   if (out_w == 0 || out_h == 0) return DFR_OK;
   FwdLaunch L{};
   L.total_tiles = P.tiles_x * P.tiles_y;
-  cudaError_t e = launch_forward(P, L, L.total_tiles, forward_threads_default(), smem_for(P),
+  L.box_floats = box_floats(P);
+  int grid = L.total_tiles;
+  if (flags & DFR_SPLIT) {
+    // persistent warps: each takes chunks of kChunk tiles
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    }
+    const int chunks = (L.total_tiles + kChunk - 1) / kChunk;
+    const int per_sm = forward_max_blocks_per_sm(P, forward_threads_default(), smem_for(P));
+    grid = std::max(1, std::min((chunks + kWarps - 1) / kWarps, sms * per_sm));
+  }
+  cudaError_t e = launch_forward(P, L, grid, forward_threads_default(), smem_for(P),
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject launch");
   return DFR_OK;
@@ -828,7 +850,7 @@ bool autotune_enabled() {
 }
 
 // Upload the frame table, zero the work counter and launch the persistent kernel.
-cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int smem, cudaStream_t s) {
+cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int floats, cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaMemcpyAsync(c.d_plans, c.h_plans, size_t(n) * sizeof(FwdPlan),
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -842,13 +864,16 @@ cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int smem, cudaStream_t 
   L.tile_start = c.d_starts;
   L.nframes = n;
   L.counter = c.d_counter;
-  return launch_forward(c.h_plans[0], L, grid, forward_threads_default(), smem, s);
+  L.box_floats = floats;
+  return launch_forward(c.h_plans[0], L, grid, forward_threads_default(),
+                        smem_for_floats(floats), s);
 }
 
 // Tile-launch autotuner: CTAs per SM of the persistent grid and TMA staging on/off, timed on
 // the caller's data (outputs are rewritten identically by every candidate).
-std::pair<int, int> autotune(DeviceCtx& c, int n, int smem, int total, cudaStream_t s) {
+std::pair<int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStream_t s) {
   const int threads = forward_threads_default();
+  const int smem = smem_for_floats(floats);
   const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
   std::vector<std::pair<int, int>> cand;
   for (int k : {1, 2, 3, 4, 6, 8})
@@ -866,13 +891,13 @@ std::pair<int, int> autotune(DeviceCtx& c, int n, int smem, int total, cudaStrea
   std::pair<int, int> pick = cand.empty() ? std::make_pair(1, 0) : cand[0];
   for (auto cd : cand) {
     for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = cd.second ? saved[f].use_tma : 0;
-    const int sm = cd.second ? smem : 0;
+    const int fl = cd.second ? floats : 0;
     const int grid = std::max(1, std::min(total, c.sms * cd.first));
     float ms = 0.f;
     bool ok = true;
     for (int rep = 0; rep < 3 && ok; ++rep) {
       if (rep == 1) cudaEventRecord(e0, s);
-      ok = enqueue_batch(c, n, grid, sm, s) == cudaSuccess;
+      ok = enqueue_batch(c, n, grid, fl, s) == cudaSuccess;
     }
     cudaEventRecord(e1, s);
     if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
@@ -907,7 +932,7 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   for (int f = 0; f < n; ++f)
     ideg = std::max(ideg, sip_round_degree(std::max(frames[f].wcs.ap_order, frames[f].wcs.bp_order)));
   int64_t total = 0;
-  int smem = 0;
+  int floats = 0;
   for (int f = 0; f < n; ++f) {
     const dfr_frame& fr = frames[f];
     rc = build_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
@@ -918,7 +943,7 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
     }
     c.h_starts[f] = int32_t(total);
     if (fr.w > 0 && fr.h > 0) total += int64_t(c.h_plans[f].tiles_x) * c.h_plans[f].tiles_y;
-    smem = std::max(smem, smem_for(c.h_plans[f]));
+    floats = std::max(floats, box_floats(c.h_plans[f]));
   }
   if (total >= (int64_t(1) << 31)) return fail(DFR_ERR_INVALID_ARG, "batch too large");
   c.h_starts[n] = int32_t(total);
@@ -930,24 +955,25 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   if (it != c.tuned.end()) {
     cfg = it->second;
   } else if (autotune_enabled()) {
-    cfg = autotune(c, n, smem, int(total), s);
+    cfg = autotune(c, n, floats, int(total), s);
     c.tuned[tkey] = cfg;
   } else {
-    cfg = {std::min(4, forward_max_blocks_per_sm(c.h_plans[0], forward_threads_default(), smem)),
-           smem > 0 ? 1 : 0};
+    cfg = {std::min(4, forward_max_blocks_per_sm(c.h_plans[0], forward_threads_default(),
+                                                 smem_for_floats(floats))),
+           floats > 0 ? 1 : 0};
   }
   if (!cfg.second) {
     for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = 0;
-    smem = 0;
+    floats = 0;
   }
   const int grid = std::max(1, std::min(int(total), c.sms * cfg.first));
-  GraphKey gk{n, order, int(flags), ideg, grid, smem, 0};
+  GraphKey gk{n, order, int(flags), ideg, grid, floats, 0};
   auto g = c.graphs.find(gk);
   if (g == c.graphs.end()) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     DFR_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_batch(c, n, grid, smem, c.cap_stream);
+    cudaError_t e = enqueue_batch(c, n, grid, floats, c.cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(c.cap_stream, &graph);
     if (e != cudaSuccess) return cuda_fail(e, "batch capture");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");

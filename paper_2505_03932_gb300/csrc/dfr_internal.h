@@ -18,11 +18,14 @@ constexpr int kMaxCoef = (DFR_MAX_SIP + 1) * (DFR_MAX_SIP + 2) / 2;  // 55
 __host__ __device__ constexpr int poly_off(int p, int n) { return p * (n + 1) - p * (p - 1) / 2; }
 __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) / 2; }
 
-// Target tile (the unit of work and the anchor cell of the split path): 64 x 16 pixels,
-// relative to the bounding-box origin.
-constexpr int kTileW = 64;
-constexpr int kTileH = 16;
+// Target tile (the unit of work of one warp and the anchor cell of the split path): 32 x 8
+// pixels, relative to the bounding-box origin. A warp takes tiles in chunks of kChunk, one
+// FP64 anchor per lane.
+constexpr int kTileW = 32;
+constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
+constexpr int kChunk = 32;
+constexpr int kWarps = 8;  // warps per CTA of the split forward kernel
 
 // Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
 struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requires
@@ -76,7 +79,7 @@ struct FwdLaunch {
   int32_t nframes;
   int32_t total_tiles;       // single frame: tiles in the grid (batch reads tile_start[n])
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
-  int32_t smem_box_floats;   // dynamic shared memory reserved for the source box
+  int32_t box_floats;        // floats per source-box buffer (2 buffers per warp), mult. of 32
 };
 
 // Backward launch arguments. The kernel accumulates parameter gradients in a padded layout
