@@ -376,7 +376,8 @@ const void* forward_kernel(const FwdPlan& p0) {
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s) {
   const void* k = forward_kernel(p0);
-  if (smem_bytes > 48 * 1024) {
+  if (smem_bytes > 0) {
+    // static + dynamic shared memory may exceed the default 48 KB window
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes);
     if (e != cudaSuccess) return e;
@@ -389,7 +390,7 @@ cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int 
 
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes) {
   const void* k = forward_kernel(p0);
-  if (smem_bytes > 48 * 1024)
+  if (smem_bytes > 0)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, size_t(smem_bytes)) !=

@@ -428,7 +428,8 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
     size_box(P);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
     const int floats = (P.box_w * P.box_h + 31) & ~31;
-    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 112 * 1024;
+    // two CTAs per SM must fit beside the ~22 KB of static shared memory per CTA
+    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 88 * 1024;
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (aligned && fits && enc) {
       cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
