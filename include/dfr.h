@@ -135,6 +135,23 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
 int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                         int32_t order, uint32_t flags, void* stream);
 
+/* dfr_reproject_batch without any device allocation: the same frames, target and flags give
+ * the same output bits as dfr_reproject_batch. The paper has no counterpart; this is for
+ * callers that cannot call cudaMalloc or let a library do it (a plug-in inside a host
+ * framework whose allocator owns all device memory; a real-time loop that must avoid
+ * cudaMalloc's implicit synchronisation). Instead of allocated scratch it uses a fixed
+ * library-owned device array of about 300 KB that every GPU loading the library keeps until
+ * the process exits. At most 64 frames per call (more -> DFR_ERR_INVALID_ARG, nothing
+ * launched). The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The frame table is
+ * copied in from a static host buffer with a pageable cudaMemcpyAsync (which waits for the
+ * stream's earlier work) and the work counter is cleared on every call. Every call shares the
+ * one array per device: calls whose kernels overlap on the GPU (different streams, or several
+ * host threads) race on it. No autotuning and no graph; caller-owned buffers as in
+ * dfr_reproject_batch. */
+int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
+                                int32_t order, uint32_t flags, void* stream);
+
 /* Adjoint of dfr_reproject with respect to the source pixels and the source WCS.
  * Given grad_out = dL/d(out) (device, out_h rows, stride go_pitch) for the same arguments as a
  * forward call, accumulates grad_src += dL/d(src_img) (device, src->naxis[1] rows, stride

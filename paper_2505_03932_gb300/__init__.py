@@ -18,7 +18,8 @@ import numpy as np
 
 __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
-    "reproject", "reproject_batch", "reproject_backward", "calculate_reprojection",
+    "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
+    "calculate_reprojection",
     "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA",
 ]
@@ -87,6 +88,9 @@ def lib():
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
             ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_void_p]
+        L.dfr_reproject_batch_noalloc.argtypes = [ctypes.POINTER(DfrFrame), ctypes.c_int32,
+                                                  ctypes.POINTER(DfrWcs), ctypes.c_int32,
+                                                  ctypes.c_uint32, ctypes.c_void_p]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
         L.dfr_device_status.argtypes = [ctypes.c_void_p]
         _LIB = L
@@ -268,6 +272,32 @@ def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear"
     _check(lib().dfr_reproject_batch(frames, n, ctypes.byref(to_c(tgt_wcs)), _order(order),
                                      _flags(precision, False, True), _stream_ptr(stream)))
     return vals, fpl
+
+
+def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=None,
+                            order="bilinear", precision="split", stream=None):
+    """dfr_reproject_batch_noalloc: the batched reprojection for callers that cannot allocate
+    device memory. The library keeps its frame table in a fixed device array (at most 64
+    frames per call) instead of calling cudaMalloc; the caller passes every image and output
+    buffer (``outs``, optional ``fps``). Returns (outs, fps)."""
+    n = len(images)
+    frames = (DfrFrame * max(n, 1))()
+    for i in range(n):
+        img = _dev_f32(images[i], "images[%d]" % i)
+        o = _dev_f32(outs[i], "outs[%d]" % i)
+        f = _dev_f32(fps[i], "fps[%d]" % i) if fps is not None else None
+        fr = frames[i]
+        fr.wcs = to_c(src_wcs_list[i])
+        fr.img = img.data_ptr()
+        fr.pitch = img.stride(0)
+        fr.out = o.data_ptr()
+        fr.footprint = f.data_ptr() if f is not None else 0
+        fr.out_pitch = o.stride(0)
+        fr.x0, fr.y0, fr.w, fr.h = (int(v) for v in bboxes[i])
+    _check(lib().dfr_reproject_batch_noalloc(frames, n, ctypes.byref(to_c(tgt_wcs)),
+                                             _order(order), _flags(precision, False, True),
+                                             _stream_ptr(stream)))
+    return outs, fps
 
 
 def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinear",

@@ -1085,3 +1085,29 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject_backward launch");
   return DFR_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Thin wrappers over the plan builder for other translation units of the library.
+namespace dfr {
+
+int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint32_t flags,
+                   int ideg, FwdPlan& P) {
+  return build_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
+                    fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, P);
+}
+
+int inverse_degree_for(const dfr_frame* frames, int n) {
+  int ideg = 0;
+  for (int f = 0; f < n; ++f)
+    ideg = std::max(ideg, sip_round_degree(std::max(frames[f].wcs.ap_order,
+                                                    frames[f].wcs.bp_order)));
+  return ideg;
+}
+
+int plan_box_floats(const FwdPlan& P) { return box_floats(P); }
+int plan_smem_bytes(int floats) { return smem_for_floats(floats); }
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int report_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+void prefix_error(const std::string& pfx) { g_err = pfx + g_err; }
+
+}  // namespace dfr

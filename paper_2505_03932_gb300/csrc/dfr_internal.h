@@ -115,4 +115,13 @@ int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd);
 int backward_threads();
 
+// Plan-builder access for translation units other than dfr_host.cpp.
+int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint32_t flags,
+                   int ideg, FwdPlan& P);
+int inverse_degree_for(const dfr_frame* frames, int n);
+int plan_box_floats(const FwdPlan& P);
+int plan_smem_bytes(int floats);
+int report_error(int code, const char* msg);
+int report_cuda_error(cudaError_t e, const char* where);
+
 }  // namespace dfr
