@@ -45,6 +45,23 @@ __device__ __forceinline__ void horner_pair(const T* __restrict__ ca, const T* _
   B = pb;
 }
 
+// The same Horner scheme for the pair (A, B) in packed FP32x2 arithmetic: c[k] = (a_k, b_k).
+// Each half runs exactly the FMA sequence of horner_pair, so the results are the same bits.
+template <int N>
+__device__ __forceinline__ float2 horner_pair2(const float2* __restrict__ c, float u, float v) {
+  const float2 uu = make_float2(u, u), vv = make_float2(v, v);
+  float2 pp = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int p = N; p >= 0; --p) {
+    const int off = poly_off(p, N);
+    float2 qq = c[off + (N - p)];
+#pragma unroll
+    for (int q = N - p - 1; q >= 0; --q) qq = __ffma2_rn(qq, vv, c[off + q]);
+    pp = (p == N) ? qq : __ffma2_rn(pp, uu, qq);
+  }
+  return pp;
+}
+
 // Runtime degree n (FP64 path and rarely used branches).
 template <typename T>
 __device__ __forceinline__ void horner_pair_rt(const T* ca, const T* cb, int n, T u, T v,
@@ -107,6 +124,29 @@ __device__ __forceinline__ void weights(T t, T* w) {
     w[1] = fma(t2, fma(T(1.5), t, T(-2.5)), T(1));
     w[2] = fma(s2, fma(T(1.5), s, T(-2.5)), T(1));
     w[3] = (T(-0.5) * t2) * s;
+  }
+}
+
+// weights() for x and y at once in packed FP32x2 arithmetic: w[k] = (wx_k, wy_k), each half
+// the same operation sequence (and bits) as weights().
+template <int ORDER>
+__device__ __forceinline__ void weights2(float2 t, float2* w) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 nt = make_float2(-t.x, -t.y);
+  if (ORDER == DFR_NEAREST) {
+    w[0] = one;
+  } else if (ORDER == DFR_BILINEAR) {
+    w[0] = __fadd2_rn(one, nt);
+    w[1] = t;
+  } else {
+    const float2 s = __fadd2_rn(one, nt);
+    const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);
+    const float2 mh = make_float2(-0.5f, -0.5f), c15 = make_float2(1.5f, 1.5f);
+    const float2 c25 = make_float2(-2.5f, -2.5f);
+    w[0] = __fmul2_rn(__fmul2_rn(mh, t), s2);
+    w[1] = __ffma2_rn(t2, __ffma2_rn(c15, t, c25), one);
+    w[2] = __ffma2_rn(s2, __ffma2_rn(c15, s, c25), one);
+    w[3] = __fmul2_rn(__fmul2_rn(mh, t2), s);
   }
 }
 
@@ -293,13 +333,18 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
 
 // FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor pixel.
 // Writes the source position relative to (bx, by); returns false if undefined.
-// IDEG > 0: unrolled inverse-SIP Horner of that degree; IDEG < 0: runtime degree; 0: none.
+// cab: the packed (AP, BP) coefficient pairs (IDEG > 0 with PAIRS: an unrolled FP32x2 Horner
+// of that degree over cab, which may live in registers; IDEG > 0 without PAIRS: the same in
+// scalar FMAs over the plan's arrays; IDEG < 0: runtime degree P.isip_deg over the plan's
+// arrays; IDEG == 0: no inverse polynomial). All forms run the same FMA sequence, so they
+// give the same bits. The rarely used target-SIP and Newton branches read the plan P.
 // geo (nullable) receives (du, dv, eu, ev) for the adjoint.
-template <int IDEG>
-__device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, float dx,
-                                             float dy, float& xr, float& yr,
-                                             float* geo = nullptr) {
-  if (P.identity) {
+template <int IDEG, bool PAIRS = true>
+__device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2* cab,
+                                                  bool identity, bool tsip, bool newton,
+                                                  const Anchor& a, float dx, float dy, float& xr,
+                                                  float& yr, float* geo = nullptr) {
+  if (identity) {
     xr = dx;
     yr = dy;
     if (geo) {
@@ -309,7 +354,7 @@ __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, 
     return true;
   }
   float dp = dx, dq = dy;
-  if (P.tsip_deg > 0) {
+  if (tsip) {
     float fa, fb;
     horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, a.tu + dx, a.tv + dy, fa, fb);
     dp = dx + (fa - a.tA);
@@ -321,20 +366,24 @@ __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, 
   const float rcp = __fdividef(1.f, den);
   float du = nu * rcp, dv = nv * rcp;
   float eu = du, ev = dv;
-  if (IDEG > 0) {
+  if (IDEG > 0 && PAIRS) {
+    const float2 g = horner_pair2<(IDEG > 0 ? IDEG : 1)>(cab, a.U0 + du, a.V0 + dv);
+    eu = du + g.x;
+    ev = dv + g.y;
+  } else if (IDEG > 0) {
+    // scalar FMAs reading the plan directly (constant-bank operands for a kernel parameter)
     float ga, gb;
     horner_pair<(IDEG > 0 ? IDEG : 1), float>(P.isip_f[0], P.isip_f[1], a.U0 + du, a.V0 + dv,
                                               ga, gb);
     eu = du + ga;
     ev = dv + gb;
   } else if (IDEG < 0 && P.isip_deg > 0) {
-    // runtime degree: the same FMA sequence as the unrolled form, so the same bits
     float ga, gb;
     horner_pair_rt<float>(P.isip_f[0], P.isip_f[1], P.isip_deg, a.U0 + du, a.V0 + dv, ga, gb);
     eu = du + ga;
     ev = dv + gb;
   }
-  if ((P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0) {
+  if (newton) {
     // Newton on e = u - U0: e + A(U0 + e) = du, started from the AP/BP estimate.
     for (int it = 0; it < P.newton_iters; ++it) {
       float A, Au, Av, B, Bu, Bv;
@@ -357,6 +406,20 @@ __device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, 
     geo[3] = ev;
   }
   return den > 0.f && a.h2 > 0.f;
+}
+
+__device__ __forceinline__ bool plan_newton(const FwdPlan& P) {
+  return (P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0;
+}
+
+// Plan-reading form (runtime degree), used where the plan is read once per pixel anyway.
+template <int IDEG>
+__device__ __forceinline__ bool split_coords(const FwdPlan& P, const Anchor& a, float dx,
+                                             float dy, float& xr, float& yr,
+                                             float* geo = nullptr) {
+  static_assert(IDEG <= 0, "the plan-reading form evaluates the inverse SIP at runtime degree");
+  return split_coords_core<IDEG>(P, nullptr, P.identity != 0, P.tsip_deg > 0, plan_newton(P), a,
+                                 dx, dy, xr, yr, geo);
 }
 
 // ---------------------------------------------------------------- TMA and mbarrier
@@ -398,6 +461,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// A tensor map that sits in global memory and was rewritten (by a copy) since the TMA unit
+// last read it must be re-acquired by the tensormap proxy before use; without this a TMA load
+// can use a stale cached descriptor from an earlier launch.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 
 // 2-D tiled TMA load of the box at (x, y) (x a multiple of 4 floats) into shared memory.

@@ -84,156 +84,263 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
 
 // ------------------------------------------------------------------ split-precision tiles
 // One warp owns a 32x8 tile: lane = column, 8 rows per lane. Per tile: source positions of the
-// 256 pixels (FP32, from the tile's FP64 anchor), warp min/max of their integer parts, one TMA
-// load of the covering source box into the warp's shared buffer, then the gather. Tiles are
-// double-buffered: the box of tile t+1 is in flight while tile t is gathered.
-struct TileCoords {
-  float x[kTileH], y[kTileH];  // source position relative to (bx, by)
-  uint32_t mask;               // covered rows of this lane
-  int32_t bx, by;              // anchor base
-  int32_t bx0, by0;            // box origin (absolute source pixel)
-  bool use_box;
+// 256 pixels in FP32 from the tile's FP64 anchor, warp min/max of their integer parts, one TMA
+// load of the covering source box into the warp's shared buffer, then the gather. Other warps
+// of the SM compute while a warp waits for its box.
+
+// The plan fields the per-pixel code reads, copied once per tile into registers (the inverse
+// SIP coefficient pairs included) so that no plan load sits in the pixel loop.
+template <int IDEG, bool PAIRS>
+struct HotPlan {
+  static constexpr int NC = (IDEG > 0 && PAIRS) ? poly_ncoef(IDEG) : 1;
+  float2 cab[NC];
+  int32_t W, H, w, h, x0, y0, box_w, box_h;
+  bool identity, tsip, newton, use_tma;
+  int64_t out_pitch;
+  float* out;
+  float* fp;
+  double* coords;
 };
 
-template <int ORDER, int IDEG>
-__device__ __forceinline__ void split_prepare(const FwdPlan& P, const Anchor& a, int local,
-                                              int lane, float* box, uint64_t* bar,
-                                              TileCoords& C) {
-  using T = Taps<ORDER>;
-  const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
-  const int gx = ox + lane;
-  const float xlo = -0.5f - float(a.bx), xhi = float(P.W) - 0.5f - float(a.bx);
-  const float ylo = -0.5f - float(a.by), yhi = float(P.H) - 0.5f - float(a.by);
-  int mnx = INT_MAX, mxx = INT_MIN, mny = INT_MAX, mxy = INT_MIN;
-  C.mask = 0;
-  C.bx = a.bx;
-  C.by = a.by;
-  const float dx = float(P.x0 + gx - a.ax);
+template <int IDEG, bool PAIRS>
+__device__ __forceinline__ void load_hot(const FwdPlan& P, HotPlan<IDEG, PAIRS>& Q) {
 #pragma unroll
-  for (int r = 0; r < kTileH; ++r) {
-    const int gy = oy + r;
-    const bool inside = gx < P.w && gy < P.h;
-    float x, y;
-    const bool ok = split_coords<IDEG>(P, a, dx, float(P.y0 + gy - a.ay), x, y);
-    C.x[r] = x;
-    C.y[r] = y;
-    if (inside && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
-      C.mask |= 1u << r;
-      const int fx = int(floorf(x)), fy = int(floorf(y));
-      mnx = min(mnx, fx);
-      mxx = max(mxx, fx);
-      mny = min(mny, fy);
-      mxy = max(mxy, fy);
-    }
-    if (P.coords && inside) {
-      double* c = P.coords + 2 * (int64_t(gy) * P.w + gx);
-      c[0] = ok ? double(a.bx) + double(x) : __longlong_as_double(0x7ff8000000000000ll);
-      c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
+  for (int k = 0; k < HotPlan<IDEG, PAIRS>::NC; ++k)
+    Q.cab[k] = (IDEG > 0 && PAIRS) ? make_float2(P.isip_f[0][k], P.isip_f[1][k])
+                                   : make_float2(0.f, 0.f);
+  Q.W = P.W;
+  Q.H = P.H;
+  Q.w = P.w;
+  Q.h = P.h;
+  Q.x0 = P.x0;
+  Q.y0 = P.y0;
+  Q.box_w = P.box_w;
+  Q.box_h = P.box_h;
+  Q.identity = P.identity != 0;
+  Q.tsip = P.tsip_deg > 0;
+  Q.newton = plan_newton(P);
+  Q.use_tma = P.use_tma != 0;
+  Q.out_pitch = P.out_pitch;
+  Q.out = P.out;
+  Q.fp = P.fp;
+  Q.coords = P.coords;
+}
+
+// Value and footprint of one pixel from its taps. S(k, q) reads tap (row k, column q) and must
+// return 0 outside the image. A pixel whose taps all lie inside the image has footprint
+// exactly 1 (the weights sum to 1) and value = sum w S; otherwise out-of-image weights are
+// zeroed, footprint = (sum wx)(sum wy) and value = sum w S / footprint. Every gather path
+// (shared-memory box, global memory, the fast tile path) runs the same operation sequence:
+// row_k = sum_q wx_q S_kq, then value = sum_k wy_k row_k, each a chain of FMAs in index order.
+template <int ORDER, bool INTERIOR, typename Tap>
+__device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by, int W, int H,
+                                               const Tap& S) {
+  using T = Taps<ORDER>;
+  const float flx = floorf(x), fly = floorf(y);
+  const float2 t = make_float2(x - flx, y - fly);
+  int ix = int(flx), iy = int(fly);
+  if (ORDER == DFR_NEAREST) {
+    ix += t.x >= 0.5f;
+    iy += t.y >= 0.5f;
+  }
+  ix += bx + T::lo;  // absolute source column / row of the first tap
+  iy += by + T::lo;
+  const bool interior = INTERIOR || (ix >= 0 && ix + T::n <= W && iy >= 0 && iy + T::n <= H);
+  float2 w[T::n];
+  weights2<ORDER>(t, w);
+  if (ORDER == DFR_NEAREST) {
+    const float v = S(ix, iy, 0, 0);
+    return interior ? make_float2(v, 1.f) : make_float2(0.f, 0.f);
+  }
+  float sx = 0.f, sy = 0.f;
+  if (!interior) {
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) {
+      w[q].x = (unsigned(ix + q) < unsigned(W)) ? w[q].x : 0.f;
+      w[q].y = (unsigned(iy + q) < unsigned(H)) ? w[q].y : 0.f;
+      sx += w[q].x;
+      sy += w[q].y;
     }
   }
-  // coverage and source extent of the tile: warp-level reductions
-  const bool any = __ballot_sync(0xffffffffu, C.mask != 0) != 0;
-  C.use_box = false;
-  C.bx0 = C.by0 = 0;
-  if (any && P.use_tma) {
-    mnx = __reduce_min_sync(0xffffffffu, mnx);
-    mxx = __reduce_max_sync(0xffffffffu, mxx);
-    mny = __reduce_min_sync(0xffffffffu, mny);
-    mxy = __reduce_max_sync(0xffffffffu, mxy);
-    C.bx0 = (a.bx + mnx + T::lo) & ~3;  // TMA x must be a multiple of 16 bytes
-    C.by0 = a.by + mny + T::lo;
-    // nearest may step one pixel up from floor(x), so its extent is two taps wide
-    constexpr int ext = (ORDER == DFR_NEAREST) ? 2 : T::n;
-    C.use_box = (a.bx + mxx + T::lo + ext - C.bx0 <= P.box_w) &&
-                (a.by + mxy + T::lo + ext - C.by0 <= P.box_h);
+  float num = 0.f;
+#pragma unroll
+  for (int k = 0; k < T::n; ++k) {
+    float row = 0.f;
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, S(ix, iy, k, q), row);
+    num = fmaf(w[k].y, row, num);
   }
-  if (C.use_box) {
+  if (interior) return make_float2(num, 1.f);
+  const float f = sx * sy;
+  if (f == 0.f) return make_float2(0.f, 0.f);
+  return make_float2((f == 1.f) ? num : __fdividef(num, f), f);
+}
+
+// Fallback gather straight from global memory (tiles whose box does not fit, or no TMA).
+template <int ORDER>
+__device__ __noinline__ float2 gather_global(const float* __restrict__ img, int64_t pitch, int W,
+                                             int H, float x, float y, int bx, int by) {
+  auto S = [=](int ix, int iy, int k, int q) -> float {
+    const int xx = ix + q, yy = iy + k;
+    return (unsigned(xx) < unsigned(W) && unsigned(yy) < unsigned(H))
+               ? __ldg(img + int64_t(yy) * pitch + xx)
+               : 0.f;
+  };
+  return interp_pixel<ORDER, false>(x, y, bx, by, W, H, S);
+}
+
+// Source box of a tile, decided from the source positions of its four corner pixels (lanes
+// 0-3) widened by the plan's curvature margin, and loaded by one TMA copy.
+struct TileBox {
+  int32_t bx0, by0;  // box origin (absolute source pixel)
+  bool use_box;      // the box was loaded (else gather from global memory)
+  bool interior;     // the widened extent lies inside the image: no tap needs masking
+  bool empty;        // the widened extent misses the image: nothing in the tile is covered
+};
+
+template <int ORDER, int IDEG, bool PAIRS>
+__device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
+                                            const Anchor& a, int ox, int oy, int lane,
+                                            float* box, uint64_t* bar, bool map_in_gmem) {
+  using T = Taps<ORDER>;
+  TileBox tb;
+  tb.bx0 = tb.by0 = 0;
+  tb.use_box = tb.interior = tb.empty = false;
+  const int cx = (lane & 1) ? min(kTileW, Q.w - ox) - 1 : 0;
+  const int cy = (lane & 2) ? min(kTileH, Q.h - oy) - 1 : 0;
+  float x = 0.f, y = 0.f;
+  bool ok = true;
+  if (lane < 4)
+    ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a,
+                                        float(Q.x0 + ox + cx - a.ax),
+                                        float(Q.y0 + oy + cy - a.ay), x, y);
+  ok = ok && fabsf(x) < 1e7f && fabsf(y) < 1e7f;
+  if (!__all_sync(0xffffffffu, ok)) return tb;  // corners undefined: gather per pixel
+  const int fx = int(floorf(x)), fy = int(floorf(y));
+  const int mnx = __reduce_min_sync(0xffffffffu, lane < 4 ? fx : INT_MAX);
+  const int mxx = __reduce_max_sync(0xffffffffu, lane < 4 ? fx : INT_MIN);
+  const int mny = __reduce_min_sync(0xffffffffu, lane < 4 ? fy : INT_MAX);
+  const int mxy = __reduce_max_sync(0xffffffffu, lane < 4 ? fy : INT_MIN);
+  const int M = P.box_margin;
+  // nearest may step one pixel up from floor(x), so its extent is two taps wide
+  constexpr int ext = (ORDER == DFR_NEAREST) ? 2 : T::n;
+  const int x_lo = a.bx + mnx - M + T::lo, x_hi = a.bx + mxx + M + T::lo + ext;  // [lo, hi)
+  const int y_lo = a.by + mny - M + T::lo, y_hi = a.by + mxy + M + T::lo + ext;
+  if (x_hi <= 0 || x_lo >= Q.W || y_hi <= 0 || y_lo >= Q.H) {
+    tb.empty = true;
+    return tb;
+  }
+  tb.interior = x_lo >= 0 && x_hi <= Q.W && y_lo >= 0 && y_hi <= Q.H;
+  if (!Q.use_tma) return tb;
+  tb.bx0 = x_lo & ~3;  // TMA x must be a multiple of 16 bytes
+  tb.by0 = y_lo;
+  tb.use_box = x_hi - tb.bx0 <= Q.box_w && y_hi - tb.by0 <= Q.box_h;
+  if (tb.use_box) {
     __syncwarp();  // every lane is done reading this buffer's previous tile
     if (lane == 0) {
       fence_proxy_async();
-      mbar_expect_tx(bar, uint32_t(P.box_w) * uint32_t(P.box_h) * 4u);
-      tma_load_2d(box, &P.tmap, bar, C.bx0, C.by0);
+      if (map_in_gmem) fence_tensormap_acquire(&P.tmap);
+      mbar_expect_tx(bar, uint32_t(Q.box_w) * uint32_t(Q.box_h) * 4u);
+      tma_load_2d(box, &P.tmap, bar, tb.bx0, tb.by0);
     }
   }
+  return tb;
 }
 
-template <int ORDER>
-__device__ __forceinline__ void split_consume(const FwdPlan& P, int local, int lane,
-                                              const float* box, uint64_t* bar, uint32_t& phase,
-                                              const TileCoords& C) {
+// Rows of one tile: per pixel the split coordinates, coverage, then the gather from the box
+// (fast when the tile is interior) or from global memory.
+template <int ORDER, int IDEG, bool PAIRS>
+__device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
+                                          const Anchor& a, int ox, int oy, int lane,
+                                          const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
-  const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
   const int gx = ox + lane;
-  bool use_box = C.use_box;
-  if (use_box) {
-    if (!mbar_wait(bar, phase)) use_box = false;  // timed out: gather from global instead
-    phase ^= 1u;
-  }
-  if (gx >= P.w) return;
-#pragma unroll
-  for (int r = 0; r < kTileH; ++r) {
-    const int gy = oy + r;
-    if (gy >= P.h) break;
-    float val = 0.f, fpv = 0.f;
-    if (C.mask & (1u << r)) {
-      const float x = C.x[r], y = C.y[r];
+  if (gx >= Q.w) return;
+  const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
+  const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
+  const float dx = float(Q.x0 + gx - a.ax);
+  const float dy0 = float(Q.y0 + oy - a.ay);
+  const int bw = Q.box_w, bh = Q.box_h;
+  const int nrows = min(kTileH, Q.h - oy);
+  float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
+  float* pf = Q.fp ? Q.fp + int64_t(oy) * Q.out_pitch + gx : nullptr;
+  const bool plain = !Q.identity && !Q.tsip && !Q.newton;
+#pragma unroll 2
+  for (int r = 0; r < nrows; ++r) {
+    float x, y;
+    const bool ok =
+        plain ? split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx,
+                                               dy0 + float(r), x, y)
+              : split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a, dx,
+                                               dy0 + float(r), x, y);
+    if (Q.coords) {
+      double* c = Q.coords + 2 * (int64_t(oy + r) * Q.w + gx);
+      c[0] = ok ? double(a.bx) + double(x) : __longlong_as_double(0x7ff8000000000000ll);
+      c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    float2 vf = make_float2(0.f, 0.f);
+    if (!tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
       const float flx = floorf(x), fly = floorf(y);
-      const float tx = x - flx, ty = y - fly;
+      const float2 t = make_float2(x - flx, y - fly);
       int ix = int(flx), iy = int(fly);
       if (ORDER == DFR_NEAREST) {
-        ix += tx >= 0.5f;
-        iy += ty >= 0.5f;
+        ix += t.x >= 0.5f;
+        iy += t.y >= 0.5f;
       }
-      ix += C.bx + T::lo;  // absolute source column / row of the first tap
-      iy += C.by + T::lo;
-      float wx[T::n], wy[T::n];
-      weights<ORDER, float>(tx, wx);
-      weights<ORDER, float>(ty, wy);
-      float sx = 0.f, sy = 0.f;
+      // first tap relative to the box origin
+      const int cx = ix + a.bx + T::lo - tb.bx0, cy = iy + a.by + T::lo - tb.by0;
+      const bool in_box = tb.use_box && cx >= 0 && cx + T::n <= bw && cy >= 0 && cy + T::n <= bh;
+      if (in_box && tb.interior) {
+        const float* b = box + cy * bw + cx;
+        if (ORDER == DFR_NEAREST) {
+          vf = make_float2(b[0], 1.f);
+        } else {
+          float2 w[T::n];
+          weights2<ORDER>(t, w);
+          float num = 0.f;
 #pragma unroll
-      for (int q = 0; q < T::n; ++q) {
-        wx[q] = (unsigned(ix + q) < unsigned(P.W)) ? wx[q] : 0.f;
-        wy[q] = (unsigned(iy + q) < unsigned(P.H)) ? wy[q] : 0.f;
-        sx += wx[q];
-        sy += wy[q];
-      }
-      float num = 0.f;
-      if (use_box) {
-        const float* b = box + (iy - C.by0) * P.box_w + (ix - C.bx0);
+          for (int k = 0; k < T::n; ++k) {
+            float row = 0.f;
 #pragma unroll
-        for (int k = 0; k < T::n; ++k) {
-          float row = 0.f;
-#pragma unroll
-          for (int q = 0; q < T::n; ++q) row = fmaf(wx[q], b[k * P.box_w + q], row);
-          num = fmaf(wy[k], row, num);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < T::n; ++k) {
-          float row = 0.f;
-          const bool iny = unsigned(iy + k) < unsigned(P.H);
-#pragma unroll
-          for (int q = 0; q < T::n; ++q) {
-            const bool in = iny && unsigned(ix + q) < unsigned(P.W);
-            const float s = in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q)) : 0.f;
-            row = fmaf(wx[q], s, row);
+            for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, b[k * bw + q], row);
+            num = fmaf(w[k].y, row, num);
           }
-          num = fmaf(wy[k], row, num);
+          vf = make_float2(num, 1.f);
         }
-      }
-      const float f = sx * sy;
-      if (f != 0.f) {
-        val = (f == 1.f) ? num : __fdividef(num, f);
-        fpv = f;
+      } else if (in_box) {
+        const int bx0 = tb.bx0, by0 = tb.by0;
+        auto SB = [=](int ixa, int iya, int k, int q) -> float {
+          return box[(iya + k - by0) * bw + (ixa + q - bx0)];
+        };
+        vf = interp_pixel<ORDER, false>(x, y, a.bx, a.by, Q.W, Q.H, SB);
+      } else {
+        vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by);
       }
     }
-    const int64_t o = int64_t(gy) * P.out_pitch + gx;
-    __stcs(P.out + o, val);
-    if (P.fp) __stcs(P.fp + o, fpv);
+    __stcs(po, vf.x);
+    po += Q.out_pitch;
+    if (pf) {
+      __stcs(pf, vf.y);
+      pf += Q.out_pitch;
+    }
   }
 }
 
 // ------------------------------------------------------------------ kernels
+// CTAs per SM the register budget targets: 3 (80 registers) for single-frame launches, whose
+// inverse-SIP coefficients are constant-bank operands; 2 (128) for batch launches, which hold
+// them in registers.
+constexpr int split_min_blocks(bool batch) { return batch ? 2 : 3; }
+
+__device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
+  int lo = 0, hi = L.nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int ORDER, int NT>
 __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ FwdPlan p0,
                                                       const FwdLaunch L) {
@@ -248,26 +355,16 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
     const int t = s_tile;
     __syncthreads();
     if (t >= L.tile_start[L.nframes]) break;
-    int lo = 0, hi = L.nframes - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    fp64_tile<ORDER, NT>(L.plans[lo], t - L.tile_start[lo]);
+    const int f = frame_of(L, t);
+    fp64_tile<ORDER, NT>(L.plans[f], t - L.tile_start[f]);
   }
 }
 
-__device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
-  int lo = 0, hi = L.nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <int ORDER, int IDEG>
-__global__ void __launch_bounds__(kWarps * 32) fwd_split_kernel(const __grid_constant__ FwdPlan p0,
+// BATCH: frame plans in global memory (persistent launch over a frame table), inverse-SIP
+// coefficients held in registers as FP32x2 pairs; otherwise one frame whose plan is the kernel
+// parameter, read as constant-bank operands by scalar FMAs (fewer registers).
+template <int ORDER, int IDEG, bool BATCH>
+__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH)) fwd_split_kernel(const __grid_constant__ FwdPlan p0,
                                                                 const FwdLaunch L) {
   extern __shared__ __align__(128) float box_raw[];
   __shared__ Anchor s_anc[kWarps][kChunk];
@@ -275,24 +372,22 @@ __global__ void __launch_bounds__(kWarps * 32) fwd_split_kernel(const __grid_con
   __shared__ int32_t s_local[kWarps][kChunk];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // two 128-byte aligned source-box buffers per warp (the launch reserves 128 bytes of slack)
-  float* box0 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(box_raw) + 127) &
-                                         ~uintptr_t(127)) + warp * 2 * L.box_floats;
-  float* box1 = box0 + L.box_floats;
-  uint64_t* bar0 = &s_bar[warp][0];
-  uint64_t* bar1 = &s_bar[warp][1];
+  // 128-byte aligned source-box buffers (the launch reserves 128 bytes of slack);
+  // indexing the shared array itself keeps the compiler on shared-memory loads
+  const int skew = int((128u - (smem_addr(box_raw) & 127u)) & 127u) / 4;
+  float* box = box_raw + skew + warp * 2 * L.box_floats;  // two buffers per warp
+  uint64_t* bar = &s_bar[warp][0];
   if (lane == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
   }
   __syncwarp();
-  uint32_t ph0 = 0, ph1 = 0;
-  const bool batch = L.plans != nullptr;
+  uint32_t phase = 0;  // bit b: parity of the next wait on buffer b
+  constexpr bool batch = BATCH;
   const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
   const int nchunks = (total + kChunk - 1) / kChunk;
-  const int stride = gridDim.x * kWarps;
-  int chunk = blockIdx.x * kWarps + warp;
-  if (batch) {
+  int chunk = blockIdx.x * kWarps + warp;  // grid launch: one chunk per warp
+  if (batch) {                             // persistent launch: chunks from a counter
     int c = 0;
     if (lane == 0) c = atomicAdd(L.counter, 1);
     chunk = __shfl_sync(0xffffffffu, c, 0);
@@ -313,37 +408,49 @@ __global__ void __launch_bounds__(kWarps * 32) fwd_split_kernel(const __grid_con
       s_local[warp][lane] = local;
     }
     __syncwarp();
-    TileCoords CA, CB;
+    // tile t's box was requested one tile earlier: TMA latency overlaps the previous tile
+    TileBox cur;
     {
       const FwdPlan& P = batch ? L.plans[s_frame[warp][0]] : p0;
-      split_prepare<ORDER, IDEG>(P, s_anc[warp][0], s_local[warp][0], lane, box0, bar0, CA);
+      HotPlan<IDEG, BATCH> Q;
+      load_hot(P, Q);
+      const Anchor a = s_anc[warp][0];
+      const int local = s_local[warp][0];
+      cur = tile_box<ORDER, IDEG, BATCH>(P, Q, a, (local % P.tiles_x) * kTileW,
+                                  (local / P.tiles_x) * kTileH, lane, box, &bar[0], batch);
     }
-    for (int t = 0; t < nt; t += 2) {
-      const FwdPlan& Pa = batch ? L.plans[s_frame[warp][t]] : p0;
+    for (int t = 0; t < nt; ++t) {
+      const int b = t & 1;
+      TileBox nxt;
+      nxt.use_box = false;
       if (t + 1 < nt) {
-        const FwdPlan& Pb = batch ? L.plans[s_frame[warp][t + 1]] : p0;
-        split_prepare<ORDER, IDEG>(Pb, s_anc[warp][t + 1], s_local[warp][t + 1], lane, box1, bar1,
-                                   CB);
+        const FwdPlan& Pn = batch ? L.plans[s_frame[warp][t + 1]] : p0;
+        HotPlan<IDEG, BATCH> Qn;
+        load_hot(Pn, Qn);
+        const Anchor an = s_anc[warp][t + 1];
+        const int ln = s_local[warp][t + 1];
+        nxt = tile_box<ORDER, IDEG, BATCH>(Pn, Qn, an, (ln % Pn.tiles_x) * kTileW,
+                                    (ln / Pn.tiles_x) * kTileH, lane, box + (b ^ 1) * L.box_floats,
+                                    &bar[b ^ 1], batch);
       }
-      split_consume<ORDER>(Pa, s_local[warp][t], lane, box0, bar0, ph0, CA);
-      if (t + 1 < nt) {
-        if (t + 2 < nt) {
-          const FwdPlan& Pc = batch ? L.plans[s_frame[warp][t + 2]] : p0;
-          split_prepare<ORDER, IDEG>(Pc, s_anc[warp][t + 2], s_local[warp][t + 2], lane, box0,
-                                     bar0, CA);
-        }
-        const FwdPlan& Pb = batch ? L.plans[s_frame[warp][t + 1]] : p0;
-        split_consume<ORDER>(Pb, s_local[warp][t + 1], lane, box1, bar1, ph1, CB);
+      const FwdPlan& P = batch ? L.plans[s_frame[warp][t]] : p0;
+      HotPlan<IDEG, BATCH> Q;
+      load_hot(P, Q);
+      const Anchor a = s_anc[warp][t];
+      const int local = s_local[warp][t];
+      if (cur.use_box) {
+        if (!mbar_wait(&bar[b], (phase >> b) & 1u)) cur.use_box = false;  // timed out
+        phase ^= 1u << b;
       }
+      tile_rows<ORDER, IDEG, BATCH>(P, Q, a, (local % P.tiles_x) * kTileW, (local / P.tiles_x) * kTileH,
+                             lane, box + b * L.box_floats, cur);
+      cur = nxt;
     }
     __syncwarp();  // anchors of this chunk are no longer read
-    if (batch) {
-      int c = 0;
-      if (lane == 0) c = atomicAdd(L.counter, 1);
-      chunk = __shfl_sync(0xffffffffu, c, 0);
-    } else {
-      chunk += stride;
-    }
+    if (!batch) break;
+    int c = 0;
+    if (lane == 0) c = atomicAdd(L.counter, 1);
+    chunk = __shfl_sync(0xffffffffu, c, 0);
   }
 }
 
@@ -351,31 +458,38 @@ __global__ void __launch_bounds__(kWarps * 32) fwd_split_kernel(const __grid_con
 constexpr int kThreads = 256;
 int forward_threads_default() { return kThreads; }
 
-template <int ORDER>
-static const void* kernel_for_order(bool split, int ideg) {
-  if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kThreads>);
+template <int ORDER, bool BATCH>
+static const void* split_for(int ideg) {
   switch (ideg) {
-    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0>);
-    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4>);
-    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6>);
-    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9>);
+    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0, BATCH>);
+    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4, BATCH>);
+    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6, BATCH>);
+    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9, BATCH>);
   }
+}
+
+template <int ORDER>
+static const void* kernel_for_order(bool split, bool batch, int ideg) {
+  if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kThreads>);
+  return batch ? split_for<ORDER, true>(ideg) : split_for<ORDER, false>(ideg);
 }
 
 // The kernel instantiation for a launch: order, flags and the packed inverse-SIP degree are
-// uniform over a launch and taken from p0.
-const void* forward_kernel(const FwdPlan& p0) {
+// uniform over a launch and taken from p0; batch launches read their plans from a table.
+static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
   const bool split = (p0.flags & DFR_SPLIT) != 0;
   switch (p0.order) {
-    case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, p0.isip_deg);
-    case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, p0.isip_deg);
-    default: return kernel_for_order<DFR_BICUBIC>(split, p0.isip_deg);
+    case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, batch, p0.isip_deg);
+    case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, batch, p0.isip_deg);
+    default: return kernel_for_order<DFR_BICUBIC>(split, batch, p0.isip_deg);
   }
 }
 
+const void* forward_kernel(const FwdPlan& p0) { return forward_kernel_for(p0, false); }
+
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s) {
-  const void* k = forward_kernel(p0);
+  const void* k = forward_kernel_for(p0, L.plans != nullptr);
   if (smem_bytes > 0) {
     // static + dynamic shared memory may exceed the default 48 KB window
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -389,7 +503,7 @@ cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int 
 }
 
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes) {
-  const void* k = forward_kernel(p0);
+  const void* k = forward_kernel_for(p0, true);
   if (smem_bytes > 0)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   int nb = 0;

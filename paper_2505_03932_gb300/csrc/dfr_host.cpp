@@ -284,11 +284,36 @@ void size_box(FwdPlan& P) {
       jxy = std::max(jxy, std::fabs(x2 - x0));
       jyy = std::max(jyy, std::fabs(y2 - y0));
     }
+  // curvature: largest second difference of the map (h = 16 px) over the same grid; a tile's
+  // source positions then stay within dev = (k_xx A^2 + 2 k_xy A B + k_yy B^2) / 8 of the
+  // bilinear interpolant of its four corners (A x B = tile extent in pixels)
+  double kxx = 0, kxy = 0, kyy = 0;
+  const double hh = 16.0;
+  for (int j = 0; j < ns; ++j)
+    for (int i = 0; i < ns; ++i) {
+      const double X = P.x0 + (P.w - 1) * double(i) / (ns - 1);
+      const double Y = P.y0 + (P.h - 1) * double(j) / (ns - 1);
+      double f[3][3][2];
+      bool ok = true;
+      for (int a = -1; a <= 1 && ok; ++a)
+        for (int b = -1; b <= 1 && ok; ++b)
+          ok = M.eval(X + a * hh, Y + b * hh, f[a + 1][b + 1][0], f[a + 1][b + 1][1]);
+      if (!ok) continue;
+      for (int c = 0; c < 2; ++c) {
+        kxx = std::max(kxx, std::fabs(f[2][1][c] - 2 * f[1][1][c] + f[0][1][c]) / (hh * hh));
+        kyy = std::max(kyy, std::fabs(f[1][2][c] - 2 * f[1][1][c] + f[1][0][c]) / (hh * hh));
+        kxy = std::max(kxy, std::fabs(f[2][2][c] - f[2][0][c] - f[0][2][c] + f[0][0][c]) /
+                                (4 * hh * hh));
+      }
+    }
+  const double A = kTileW - 1, B = kTileH - 1;
+  const double dev = (kxx * A * A + 2 * kxy * A * B + kyy * B * B) / 8.0;
+  P.box_margin = 1 + int(std::ceil(4.0 * dev));
   const int ext = (P.order == DFR_BICUBIC) ? 4 : 2;
   const double sx = 1.1 * (jxx * (kTileW - 1) + jxy * (kTileH - 1)) + 1.0;
   const double sy = 1.1 * (jyx * (kTileW - 1) + jyy * (kTileH - 1)) + 1.0;
-  int bw = int(std::ceil(sx)) + 1 + ext + 3;
-  int bh = int(std::ceil(sy)) + 1 + ext;
+  int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
+  int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
   bw = (bw + 3) & ~3;
   P.box_w = bw;
   P.box_h = bh;
@@ -428,8 +453,8 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
     size_box(P);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
     const int floats = (P.box_w * P.box_h + 31) & ~31;
-    // two CTAs per SM must fit beside the ~22 KB of static shared memory per CTA
-    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 88 * 1024;
+    // several CTAs per SM must fit beside their static shared memory
+    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 64 * 1024;
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (aligned && fits && enc) {
       cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
@@ -805,17 +830,9 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
   L.box_floats = box_floats(P);
   int grid = L.total_tiles;
   if (flags & DFR_SPLIT) {
-    // persistent warps: each takes chunks of kChunk tiles
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 1;
-    }
+    // one chunk of kChunk tiles per warp
     const int chunks = (L.total_tiles + kChunk - 1) / kChunk;
-    const int per_sm = forward_max_blocks_per_sm(P, forward_threads_default(), smem_for(P));
-    grid = std::max(1, std::min((chunks + kWarps - 1) / kWarps, sms * per_sm));
+    grid = (chunks + kWarps - 1) / kWarps;
   }
   cudaError_t e = launch_forward(P, L, grid, forward_threads_default(), smem_for(P),
                                  static_cast<cudaStream_t>(stream));

@@ -19,12 +19,12 @@ __host__ __device__ constexpr int poly_off(int p, int n) { return p * (n + 1) - 
 __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) / 2; }
 
 // Target tile (the unit of work of one warp and the anchor cell of the split path): 32 x 8
-// pixels, relative to the bounding-box origin. A warp takes tiles in chunks of kChunk, one
-// FP64 anchor per lane.
+// pixels, relative to the bounding-box origin. A warp takes tiles in chunks of kChunk; the
+// chunk's FP64 anchors are computed in parallel, one per lane.
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
-constexpr int kChunk = 32;
+constexpr int kChunk = 4;
 constexpr int kWarps = 8;  // warps per CTA of the split forward kernel
 
 // Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
@@ -43,6 +43,7 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   int64_t pitch;
   int32_t W, H;
   int32_t use_tma, box_w, box_h;
+  int32_t box_margin;        // px added around a tile's corner extent (covers map curvature)
   int32_t identity;          // source and target WCS are bitwise equal
   // target WCS
   double crpix_t[2];         // CRPIX - 1 (0-based reference pixel)
@@ -79,7 +80,7 @@ struct FwdLaunch {
   int32_t nframes;
   int32_t total_tiles;       // single frame: tiles in the grid (batch reads tile_start[n])
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
-  int32_t box_floats;        // floats per source-box buffer (2 buffers per warp), mult. of 32
+  int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
 };
 
 // Backward launch arguments. The kernel accumulates parameter gradients in a padded layout
