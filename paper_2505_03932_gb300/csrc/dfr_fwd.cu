@@ -193,6 +193,7 @@ __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int6
 // 0-3) widened by the plan's curvature margin, and loaded by one TMA copy.
 struct TileBox {
   int32_t bx0, by0;  // box origin (absolute source pixel)
+  int32_t ex0, ey0, ew, eh;  // widened corner extent of the tile's taps, [ex0, ex0 + ew) etc.
   bool use_box;      // the box was loaded (else gather from global memory)
   bool interior;     // the widened extent lies inside the image: no tap needs masking
   bool empty;        // the widened extent misses the image: nothing in the tile is covered
@@ -205,6 +206,7 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG
   using T = Taps<ORDER>;
   TileBox tb;
   tb.bx0 = tb.by0 = 0;
+  tb.ex0 = tb.ey0 = tb.ew = tb.eh = 0;
   tb.use_box = tb.interior = tb.empty = false;
   const int cx = (lane & 1) ? min(kTileW, Q.w - ox) - 1 : 0;
   const int cy = (lane & 2) ? min(kTileH, Q.h - oy) - 1 : 0;
@@ -231,6 +233,10 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG
     return tb;
   }
   tb.interior = x_lo >= 0 && x_hi <= Q.W && y_lo >= 0 && y_hi <= Q.H;
+  tb.ex0 = x_lo;
+  tb.ey0 = y_lo;
+  tb.ew = x_hi - x_lo;
+  tb.eh = y_hi - y_lo;
   if (!Q.use_tma) return tb;
   tb.bx0 = x_lo & ~3;  // TMA x must be a multiple of 16 bytes
   tb.by0 = y_lo;
@@ -249,11 +255,90 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG
 
 // Rows of one tile: per pixel the split coordinates, coverage, then the gather from the box
 // (fast when the tile is interior) or from global memory.
+// Fast rows: the tile lies inside the bounding box, its widened source extent inside the image
+// and inside the loaded box, and the plan has no target SIP, Newton inverse or identity. No
+// per-pixel branch: taps are read from the box at clamped positions and the rare pixel whose
+// taps leave the box (the curvature margin was too small) is redone from global memory.
+template <int ORDER, int IDEG, bool PAIRS>
+__device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
+                                               const Anchor& a, int ox, int oy, int lane,
+                                               const float* box, const TileBox& tb) {
+  using T = Taps<ORDER>;
+  const int gx = ox + lane;
+  const float dx = float(Q.x0 + gx - a.ax);
+  float dy = float(Q.y0 + oy - a.ay);
+  const int bw = Q.box_w;
+  // a pixel is taken here only if all its taps lie in the widened extent, which is inside the
+  // image (no masking, footprint 1) and inside the box
+  const unsigned uxmax = unsigned(tb.ew - T::n), uymax = unsigned(tb.eh - T::n);
+  const int ux0 = a.bx + T::lo - tb.ex0, uy0 = a.by + T::lo - tb.ey0;
+  const int sx0 = tb.ex0 - tb.bx0, sy0 = tb.ey0 - tb.by0;  // extent origin within the box
+  float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
+  float* pf = Q.fp ? Q.fp + int64_t(oy) * Q.out_pitch + gx : nullptr;
+  uint32_t bad = 0;
+#pragma unroll
+  for (int r = 0; r < kTileH; ++r) {
+    float x, y;
+    const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx, dy, x, y);
+    const float flx = floorf(x), fly = floorf(y);
+    const float2 t = make_float2(x - flx, y - fly);
+    int ux = int(flx) + ux0, uy = int(fly) + uy0;
+    if (ORDER == DFR_NEAREST) {
+      ux += t.x >= 0.5f;
+      uy += t.y >= 0.5f;
+    }
+    const bool in_ext = ok && unsigned(ux) <= uxmax && unsigned(uy) <= uymax;
+    bad |= uint32_t(!in_ext) << r;
+    const float* b = box + ((in_ext ? uy : 0) + sy0) * bw + (in_ext ? ux : 0) + sx0;
+    float num;
+    if (ORDER == DFR_NEAREST) {
+      num = b[0];
+    } else {
+      float2 w[T::n];
+      weights2<ORDER>(t, w);
+      num = 0.f;
+#pragma unroll
+      for (int k = 0; k < T::n; ++k) {
+        float row = 0.f;
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, b[k * bw + q], row);
+        num = fmaf(w[k].y, row, num);
+      }
+    }
+    __stcs(po + int64_t(r) * Q.out_pitch, num);
+    if (pf) __stcs(pf + int64_t(r) * Q.out_pitch, 1.f);
+    dy += 1.f;
+  }
+  if (__any_sync(0xffffffffu, bad != 0) && bad) {
+    // pixels outside the box: the general per-pixel path, from global memory
+    const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
+    const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
+    for (int r = 0; r < kTileH; ++r) {
+      if (!((bad >> r) & 1u)) continue;
+      float x, y;
+      const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx,
+                                                     float(Q.y0 + oy - a.ay) + float(r), x, y);
+      float2 vf = make_float2(0.f, 0.f);
+      if (ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi)
+        vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by);
+      __stcs(po + int64_t(r) * Q.out_pitch, vf.x);
+      if (pf) __stcs(pf + int64_t(r) * Q.out_pitch, vf.y);
+    }
+  }
+}
+
+// General rows: per pixel the split coordinates, coverage, then the gather from the box (when
+// its taps are in the box) or from global memory.
 template <int ORDER, int IDEG, bool PAIRS>
 __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
                                           const Anchor& a, int ox, int oy, int lane,
                                           const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
+  const bool plain = !Q.identity && !Q.tsip && !Q.newton;
+  if (plain && tb.use_box && tb.interior && ox + kTileW <= Q.w && oy + kTileH <= Q.h) {
+    tile_rows_fast<ORDER, IDEG, PAIRS>(P, Q, a, ox, oy, lane, box, tb);
+    return;
+  }
   const int gx = ox + lane;
   if (gx >= Q.w) return;
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
@@ -264,20 +349,11 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
   const int nrows = min(kTileH, Q.h - oy);
   float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
   float* pf = Q.fp ? Q.fp + int64_t(oy) * Q.out_pitch + gx : nullptr;
-  const bool plain = !Q.identity && !Q.tsip && !Q.newton;
-#pragma unroll 2
+#pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
     float x, y;
-    const bool ok =
-        plain ? split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx,
-                                               dy0 + float(r), x, y)
-              : split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a, dx,
-                                               dy0 + float(r), x, y);
-    if (Q.coords) {
-      double* c = Q.coords + 2 * (int64_t(oy + r) * Q.w + gx);
-      c[0] = ok ? double(a.bx) + double(x) : __longlong_as_double(0x7ff8000000000000ll);
-      c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
-    }
+    const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a,
+                                                   dx, dy0 + float(r), x, y);
     float2 vf = make_float2(0.f, 0.f);
     if (!tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
       const float flx = floorf(x), fly = floorf(y);
@@ -290,24 +366,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
       // first tap relative to the box origin
       const int cx = ix + a.bx + T::lo - tb.bx0, cy = iy + a.by + T::lo - tb.by0;
       const bool in_box = tb.use_box && cx >= 0 && cx + T::n <= bw && cy >= 0 && cy + T::n <= bh;
-      if (in_box && tb.interior) {
-        const float* b = box + cy * bw + cx;
-        if (ORDER == DFR_NEAREST) {
-          vf = make_float2(b[0], 1.f);
-        } else {
-          float2 w[T::n];
-          weights2<ORDER>(t, w);
-          float num = 0.f;
-#pragma unroll
-          for (int k = 0; k < T::n; ++k) {
-            float row = 0.f;
-#pragma unroll
-            for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, b[k * bw + q], row);
-            num = fmaf(w[k].y, row, num);
-          }
-          vf = make_float2(num, 1.f);
-        }
-      } else if (in_box) {
+      if (in_box) {
         const int bx0 = tb.bx0, by0 = tb.by0;
         auto SB = [=](int ixa, int iya, int k, int q) -> float {
           return box[(iya + k - by0) * bw + (ixa + q - bx0)];
@@ -324,6 +383,40 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
       pf += Q.out_pitch;
     }
   }
+}
+
+// Source positions exactly as the split kernels compute them (same anchors, same arithmetic),
+// for the coordinate output of dfr_reproject; one thread per target pixel.
+template <int IDEG>
+__global__ void __launch_bounds__(256) split_coords_kernel(const __grid_constant__ FwdPlan P) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(P.w) * P.h) return;
+  const int gx = int(i % P.w), gy = int(i / P.w);
+  const int ox = gx - gx % kTileW, oy = gy - gy % kTileH;
+  Anchor a;
+  make_anchor(P, P.x0 + ox + kTileW / 2, P.y0 + oy + kTileH / 2, a);
+  float x, y;
+  const bool ok = split_coords_core<IDEG, false>(P, nullptr, P.identity != 0, P.tsip_deg > 0,
+                                                 plan_newton(P), a, float(P.x0 + gx - a.ax),
+                                                 float(P.y0 + gy - a.ay), x, y);
+  double* c = P.coords + 2 * i;
+  c[0] = ok ? double(a.bx) + double(x) : __longlong_as_double(0x7ff8000000000000ll);
+  c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s) {
+  const int64_t n = int64_t(p0.w) * p0.h;
+  const int grid = int((n + 255) / 256);
+  FwdPlan p = p0;
+  void* args[] = {&p};
+  const void* k;
+  switch (p0.isip_deg) {
+    case 0: k = reinterpret_cast<const void*>(&split_coords_kernel<0>); break;
+    case 4: k = reinterpret_cast<const void*>(&split_coords_kernel<4>); break;
+    case 6: k = reinterpret_cast<const void*>(&split_coords_kernel<6>); break;
+    default: k = reinterpret_cast<const void*>(&split_coords_kernel<9>); break;
+  }
+  return cudaLaunchKernel(k, dim3(grid), dim3(256), args, 0, s);
 }
 
 // ------------------------------------------------------------------ kernels

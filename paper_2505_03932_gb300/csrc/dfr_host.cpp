@@ -834,9 +834,16 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
     const int chunks = (L.total_tiles + kChunk - 1) / kChunk;
     grid = (chunks + kWarps - 1) / kWarps;
   }
-  cudaError_t e = launch_forward(P, L, grid, forward_threads_default(), smem_for(P),
+  // the split kernels leave the coordinate output to a separate kernel (same arithmetic)
+  FwdPlan Pk = P;
+  if (flags & DFR_SPLIT) Pk.coords = nullptr;
+  cudaError_t e = launch_forward(Pk, L, grid, forward_threads_default(), smem_for(P),
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject launch");
+  if ((flags & DFR_SPLIT) && coords_out) {
+    e = launch_split_coords(P, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject coordinate launch");
+  }
   return DFR_OK;
 }
 

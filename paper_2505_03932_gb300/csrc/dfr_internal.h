@@ -107,6 +107,7 @@ enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s);
 const void* forward_kernel(const FwdPlan& p0);
+cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s);
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
 int forward_threads_default();
 cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
