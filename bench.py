@@ -148,9 +148,10 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    src, tgt, img = workload()
-    src, fit_max, fit_rms = dfr.fit_inverse_sip(src, 4)
-    H, W = tgt["naxis"][1], tgt["naxis"][0]
+    src_rec, tgt_rec, img = workload()
+    src, fit_max, fit_rms = dfr.fit_inverse_sip(src_rec, 4)
+    src, tgt = dfr.to_c(src), dfr.to_c(tgt_rec)  # marshal the WCS records once
+    H, W = tgt.naxis[1], tgt.naxis[0]
     npix = H * W
     img_d = torch.from_numpy(img).to(dev)
     out = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -241,9 +242,9 @@ def run_gpu(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        o_src = oracle_wcs(workload()[0])
+        o_src = oracle_wcs(src_rec)
         npx = 100000
-        secs = oracle_sample_rate(o_src, tgt, img, npx)
+        secs = oracle_sample_rate(o_src, tgt_rec, img, npx)
         cpu = {"value": npx / secs / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                "sample": "%d random target pixels of the 4096^2 frame (%.1f s)" % (npx, secs)}
 

@@ -28,7 +28,7 @@ NEAREST, BILINEAR, BICUBIC = 0, 1, 2
 FP64, SPLIT, EXACT_INVERSE, NO_TMA = 0, 1, 2, 4
 ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC}
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIBPATH = os.path.join(_HERE, "libdfr.so")
+_LIBPATH = os.environ.get("DFR_LIBRARY") or os.path.join(_HERE, "libdfr.so")
 
 
 class DfrError(RuntimeError):
@@ -220,7 +220,8 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
     src_img = _dev_f32(src_img, "src_img")
     if bbox is None:
         if shape_out is None:
-            shape_out = (int(tgt_wcs["naxis"][1]), int(tgt_wcs["naxis"][0]))
+            nax = tgt_wcs.naxis if isinstance(tgt_wcs, DfrWcs) else tgt_wcs["naxis"]
+            shape_out = (int(nax[1]), int(nax[0]))
         bbox = (0, 0, int(shape_out[1]), int(shape_out[0]))
     x0, y0, w, h = (int(v) for v in bbox)
     dev = src_img.device

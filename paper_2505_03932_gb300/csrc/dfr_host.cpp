@@ -540,6 +540,78 @@ int ensure_ctx(DeviceCtx*& out, size_t nframes) {
   return DFR_OK;
 }
 
+// Small cache of built plans: repeated calls with identical arguments (the common case of a
+// pipeline reprojecting into the same buffers) skip the host plan build (box sizing samples
+// the map a few thousand times).
+struct PlanKey {
+  dfr_wcs src, tgt;
+  const float* img;
+  int64_t pitch;
+  float* out;
+  float* fp;
+  int64_t out_pitch;
+  int32_t x0, y0, w, h, order;
+  uint32_t flags;
+  double* coords;
+  int device;
+};
+
+struct PlanEntry {
+  PlanKey key;
+  FwdPlan plan;
+  uint64_t used;
+};
+
+std::mutex g_plan_mu;
+std::vector<PlanEntry> g_plans;
+uint64_t g_plan_clock = 0;
+constexpr size_t kPlanCacheSize = 8;
+
+int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
+                float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
+                int32_t h, int32_t order, uint32_t flags, double* coords, FwdPlan& P) {
+  if (!src || !tgt) return build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h,
+                                      order, flags, coords, -1, P);
+  PlanKey k;
+  std::memset(&k, 0, sizeof(k));
+  k.src = *src;
+  k.tgt = *tgt;
+  k.img = img;
+  k.pitch = pitch;
+  k.out = out;
+  k.fp = fp;
+  k.out_pitch = out_pitch;
+  k.x0 = x0;
+  k.y0 = y0;
+  k.w = w;
+  k.h = h;
+  k.order = order;
+  k.flags = flags;
+  k.coords = coords;
+  if (cudaGetDevice(&k.device) != cudaSuccess) k.device = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (PlanEntry& e : g_plans)
+      if (std::memcmp(&e.key, &k, sizeof(k)) == 0) {
+        e.used = ++g_plan_clock;
+        P = e.plan;
+        return DFR_OK;
+      }
+  }
+  int rc = build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h, order, flags,
+                      coords, -1, P);
+  if (rc != DFR_OK) return rc;
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  if (g_plans.size() < kPlanCacheSize) {
+    g_plans.push_back(PlanEntry{k, P, ++g_plan_clock});
+  } else {
+    auto lru = std::min_element(g_plans.begin(), g_plans.end(),
+                                [](const PlanEntry& a, const PlanEntry& b) { return a.used < b.used; });
+    *lru = PlanEntry{k, P, ++g_plan_clock};
+  }
+  return DFR_OK;
+}
+
 }  // namespace
 }  // namespace dfr
 
@@ -821,8 +893,8 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
                   int32_t y0, int32_t out_w, int32_t out_h, int32_t order, uint32_t flags,
                   double* coords_out, void* stream) {
   FwdPlan P;
-  int rc = build_plan(src, tgt, src_img, src_pitch, out, footprint, out_pitch, x0, y0, out_w,
-                      out_h, order, flags, coords_out, -1, P);
+  int rc = cached_plan(src, tgt, src_img, src_pitch, out, footprint, out_pitch, x0, y0, out_w,
+                       out_h, order, flags, coords_out, P);
   if (rc != DFR_OK) return rc;
   if (out_w == 0 || out_h == 0) return DFR_OK;
   FwdLaunch L{};
