@@ -252,6 +252,8 @@ def run_gpu(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "ms_per_step_median": float(np.median(times)),
+            "ms_steps": [round(float(t), 4) for t in times],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "split", "output_mpix": npix / 1e6,
