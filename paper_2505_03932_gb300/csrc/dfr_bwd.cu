@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ox = (tile % P.tiles_x) * kTileW, oy = (tile / P.tiles_x) * kTileH;
-    const int ax = P.x0 + ox + kTileW / 2, ay = P.y0 + oy + kTileH / 2;
+    const int ax = cell_anchor_x(P, ox), ay = cell_anchor_y(P, oy);
     if (split) {
       if (tid == 0) make_anchor(P, ax, ay, sanc);
       __syncthreads();

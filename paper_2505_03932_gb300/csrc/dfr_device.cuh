@@ -292,6 +292,8 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
     a.tu = a.tv = a.tA = a.tB = 0.f;
     return;
   }
+  // FP64 only where absolute positions need it: the homography at the anchor and the anchor's
+  // source position; the local expansion coefficients follow in FP32
   const double u = double(ax) - P.crpix_t[0];
   const double v = double(ay) - P.crpix_t[1];
   double p = u, q = v;
@@ -308,19 +310,25 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
     a.tA = ga;
     a.tB = gb;
   }
-  const double h0 = P.G[0][0] * p + P.G[0][1] * q + P.G[0][2];
-  const double h1 = P.G[1][0] * p + P.G[1][1] * q + P.G[1][2];
-  const double h2 = P.G[2][0] * p + P.G[2][1] * q + P.G[2][2];
-  const double U0 = h0 / h2, V0 = h1 / h2;
-  a.a0 = float(P.G[0][0] - U0 * P.G[2][0]);
-  a.a1 = float(P.G[0][1] - U0 * P.G[2][1]);
-  a.b0 = float(P.G[1][0] - V0 * P.G[2][0]);
-  a.b1 = float(P.G[1][1] - V0 * P.G[2][1]);
-  a.g20 = float(P.G[2][0]);
-  a.g21 = float(P.G[2][1]);
+  const double h0 = fma(P.G[0][0], p, fma(P.G[0][1], q, P.G[0][2]));
+  const double h1 = fma(P.G[1][0], p, fma(P.G[1][1], q, P.G[1][2]));
+  const double h2 = fma(P.G[2][0], p, fma(P.G[2][1], q, P.G[2][2]));
+  // 1/h2: FP32 estimate refined by two Newton steps to full FP64 accuracy
+  double r = double(__frcp_rn(float(h2)));
+  r = fma(r, fma(-h2, r, 1.0), r);
+  r = fma(r, fma(-h2, r, 1.0), r);
+  const double U0 = h0 * r, V0 = h1 * r;
+  const float U0f = float(U0), V0f = float(V0);
+  const float g20 = float(P.G[2][0]), g21 = float(P.G[2][1]);
+  a.a0 = fmaf(-U0f, g20, float(P.G[0][0]));
+  a.a1 = fmaf(-U0f, g21, float(P.G[0][1]));
+  a.b0 = fmaf(-V0f, g20, float(P.G[1][0]));
+  a.b1 = fmaf(-V0f, g21, float(P.G[1][1]));
+  a.g20 = g20;
+  a.g21 = g21;
   a.h2 = float(h2);
-  a.U0 = float(U0);
-  a.V0 = float(V0);
+  a.U0 = U0f;
+  a.V0 = V0f;
   const double X0 = U0 + P.crpix_s[0], Y0 = V0 + P.crpix_s[1];
   const double fx = floor(X0), fy = floor(Y0);
   const bool finite = isfinite(X0) && isfinite(Y0) && fabs(X0) < 1e9 && fabs(Y0) < 1e9;
@@ -328,7 +336,16 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
   a.by = finite ? int32_t(fy) : 0;
   a.f0x = finite ? float(X0 - fx) : 0.f;
   a.f0y = finite ? float(Y0 - fy) : 0.f;
-  if (!finite || !(h2 > 0.0)) a.h2 = -1.f;  // the whole tile is treated as uncovered
+  if (!finite || !(h2 > 0.0)) a.h2 = -1.f;  // the whole cell is treated as uncovered
+}
+
+// Anchor pixel (absolute target coordinates) of the 32x32 cell that holds bounding-box pixel
+// (gx, gy): the cell centre.
+__device__ __forceinline__ int cell_anchor_x(const FwdPlan& P, int gx) {
+  return P.x0 + (gx - gx % kCellW) + kCellW / 2;
+}
+__device__ __forceinline__ int cell_anchor_y(const FwdPlan& P, int gy) {
+  return P.y0 + (gy - gy % kCellH) + kCellH / 2;
 }
 
 // FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor pixel.

@@ -83,10 +83,9 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
 }
 
 // ------------------------------------------------------------------ split-precision tiles
-// One warp owns a 32x8 tile: lane = column, 8 rows per lane. Per tile: source positions of the
-// 256 pixels in FP32 from the tile's FP64 anchor, warp min/max of their integer parts, one TMA
-// load of the covering source box into the warp's shared buffer, then the gather. Other warps
-// of the SM compute while a warp waits for its box.
+// One warp owns a 32x8 tile at a time: lane = column, 8 rows per lane. Per pixel the source
+// position comes in FP32 from the FP64 anchor of the pixel's 32x32 cell; per tile a TMA load
+// stages the source box covering the tile's taps in the warp's shared buffer.
 
 // The plan fields the per-pixel code reads, copied once per tile into registers (the inverse
 // SIP coefficient pairs included) so that no plan load sits in the pixel loop.
@@ -208,6 +207,10 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG
   tb.bx0 = tb.by0 = 0;
   tb.ex0 = tb.ey0 = tb.ew = tb.eh = 0;
   tb.use_box = tb.interior = tb.empty = false;
+  if (ox >= Q.w || oy >= Q.h) {  // a cell's tile below the bounding box
+    tb.empty = true;
+    return tb;
+  }
   const int cx = (lane & 1) ? min(kTileW, Q.w - ox) - 1 : 0;
   const int cy = (lane & 2) ? min(kTileH, Q.h - oy) - 1 : 0;
   float x = 0.f, y = 0.f;
@@ -334,6 +337,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
                                           const Anchor& a, int ox, int oy, int lane,
                                           const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
+  if (oy >= Q.h) return;
   const bool plain = !Q.identity && !Q.tsip && !Q.newton;
   if (plain && tb.use_box && tb.interior && ox + kTileW <= Q.w && oy + kTileH <= Q.h) {
     tile_rows_fast<ORDER, IDEG, PAIRS>(P, Q, a, ox, oy, lane, box, tb);
@@ -392,9 +396,8 @@ __global__ void __launch_bounds__(256) split_coords_kernel(const __grid_constant
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= int64_t(P.w) * P.h) return;
   const int gx = int(i % P.w), gy = int(i / P.w);
-  const int ox = gx - gx % kTileW, oy = gy - gy % kTileH;
   Anchor a;
-  make_anchor(P, P.x0 + ox + kTileW / 2, P.y0 + oy + kTileH / 2, a);
+  make_anchor(P, cell_anchor_x(P, gx), cell_anchor_y(P, gy), a);
   float x, y;
   const bool ok = split_coords_core<IDEG, false>(P, nullptr, P.identity != 0, P.tsip_deg > 0,
                                                  plan_newton(P), a, float(P.x0 + gx - a.ax),
@@ -420,10 +423,10 @@ cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ kernels
-// CTAs per SM the register budget targets: 3 (80 registers) for single-frame launches, whose
-// inverse-SIP coefficients are constant-bank operands; 2 (128) for batch launches, which hold
-// them in registers.
-constexpr int split_min_blocks(bool batch) { return batch ? 2 : 3; }
+// CTAs (of kWarps warps) per SM the register budget targets: 6 (80 registers) for single-frame
+// launches, whose inverse-SIP coefficients are constant-bank operands; 4 (128) for batch
+// launches, which hold them in registers.
+constexpr int split_min_blocks(bool batch) { return batch ? 4 : 6; }
 
 __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
   int lo = 0, hi = L.nframes - 1;
@@ -456,17 +459,22 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
 // BATCH: frame plans in global memory (persistent launch over a frame table), inverse-SIP
 // coefficients held in registers as FP32x2 pairs; otherwise one frame whose plan is the kernel
 // parameter, read as constant-bank operands by scalar FMAs (fewer registers).
+//
+// Work unit: kCellsPerCta consecutive 32x32 anchor cells. Warp 0 computes their FP64 anchors
+// (one lane per cell), then each warp processes the 4 tiles of each of its kCellsPerWarp cells,
+// requesting the source box of the next tile before gathering the current one.
 template <int ORDER, int IDEG, bool BATCH>
-__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH)) fwd_split_kernel(const __grid_constant__ FwdPlan p0,
-                                                                const FwdLaunch L) {
+__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH)) fwd_split_kernel(
+    const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
   extern __shared__ __align__(128) float box_raw[];
-  __shared__ Anchor s_anc[kWarps][kChunk];
-  __shared__ int32_t s_frame[kWarps][kChunk];
-  __shared__ int32_t s_local[kWarps][kChunk];
+  __shared__ Anchor s_anc[kCellsPerCta];
+  __shared__ int32_t s_frame[kCellsPerCta];
+  __shared__ int32_t s_cell[kCellsPerCta];
   __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+  __shared__ int32_t s_unit;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // 128-byte aligned source-box buffers (the launch reserves 128 bytes of slack);
-  // indexing the shared array itself keeps the compiler on shared-memory loads
+  // 128-byte aligned source-box buffers (the launch reserves 128 bytes of slack); indexing the
+  // shared array itself keeps the compiler on shared-memory loads
   const int skew = int((128u - (smem_addr(box_raw) & 127u)) & 127u) / 4;
   float* box = box_raw + skew + warp * 2 * L.box_floats;  // two buffers per warp
   uint64_t* bar = &s_bar[warp][0];
@@ -474,76 +482,84 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH)) fwd_spli
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
   }
-  __syncwarp();
   uint32_t phase = 0;  // bit b: parity of the next wait on buffer b
   constexpr bool batch = BATCH;
-  const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
-  const int nchunks = (total + kChunk - 1) / kChunk;
-  int chunk = blockIdx.x * kWarps + warp;  // grid launch: one chunk per warp
-  if (batch) {                             // persistent launch: chunks from a counter
-    int c = 0;
-    if (lane == 0) c = atomicAdd(L.counter, 1);
-    chunk = __shfl_sync(0xffffffffu, c, 0);
+  const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;  // cells
+  const int nunits = (total + kCellsPerCta - 1) / kCellsPerCta;
+  int unit = blockIdx.x;  // grid launch: one unit per CTA; persistent: units from a counter
+  if (batch) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
+    __syncthreads();
+    unit = s_unit;
   }
-  while (chunk < nchunks) {
-    const int t0 = chunk * kChunk;
-    const int nt = min(kChunk, total - t0);
-    if (lane < nt) {  // FP64 anchors of the chunk's tiles, one per lane
-      int f = 0, local = t0 + lane;
+  while (unit < nunits) {
+    const int c0 = unit * kCellsPerCta;
+    const int nc = min(kCellsPerCta, total - c0);
+    if (warp == 0 && lane < nc) {  // FP64 anchors of the unit's cells, one per lane
+      int f = 0, cell = c0 + lane;
       if (batch) {
-        f = frame_of(L, local);
-        local -= L.tile_start[f];
+        f = frame_of(L, cell);
+        cell -= L.tile_start[f];
       }
       const FwdPlan& P = batch ? L.plans[f] : p0;
-      const int ox = (local % P.tiles_x) * kTileW, oy = (local / P.tiles_x) * kTileH;
-      make_anchor(P, P.x0 + ox + kTileW / 2, P.y0 + oy + kTileH / 2, s_anc[warp][lane]);
-      s_frame[warp][lane] = f;
-      s_local[warp][lane] = local;
+      const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
+      make_anchor(P, P.x0 + cox + kCellW / 2, P.y0 + coy + kCellH / 2, s_anc[lane]);
+      s_frame[lane] = f;
+      s_cell[lane] = cell;
     }
-    __syncwarp();
-    // tile t's box was requested one tile earlier: TMA latency overlaps the previous tile
-    TileBox cur;
-    {
-      const FwdPlan& P = batch ? L.plans[s_frame[warp][0]] : p0;
-      HotPlan<IDEG, BATCH> Q;
-      load_hot(P, Q);
-      const Anchor a = s_anc[warp][0];
-      const int local = s_local[warp][0];
-      cur = tile_box<ORDER, IDEG, BATCH>(P, Q, a, (local % P.tiles_x) * kTileW,
-                                  (local / P.tiles_x) * kTileH, lane, box, &bar[0], batch);
-    }
-    for (int t = 0; t < nt; ++t) {
-      const int b = t & 1;
-      TileBox nxt;
-      nxt.use_box = false;
-      if (t + 1 < nt) {
-        const FwdPlan& Pn = batch ? L.plans[s_frame[warp][t + 1]] : p0;
-        HotPlan<IDEG, BATCH> Qn;
-        load_hot(Pn, Qn);
-        const Anchor an = s_anc[warp][t + 1];
-        const int ln = s_local[warp][t + 1];
-        nxt = tile_box<ORDER, IDEG, BATCH>(Pn, Qn, an, (ln % Pn.tiles_x) * kTileW,
-                                    (ln / Pn.tiles_x) * kTileH, lane, box + (b ^ 1) * L.box_floats,
-                                    &bar[b ^ 1], batch);
+    __syncthreads();
+    // this warp's tiles: kTilesPerCell per cell, cells warp*kCellsPerWarp ...
+    const int j0 = warp * kCellsPerWarp;
+    const int ncw = max(0, min(kCellsPerWarp, nc - j0));
+    const int nt = ncw * kTilesPerCell;
+    if (nt > 0) {
+      TileBox cur;
+      {
+        const FwdPlan& P = batch ? L.plans[s_frame[j0]] : p0;
+        HotPlan<IDEG, BATCH> Q;
+        load_hot(P, Q);
+        const Anchor a = s_anc[j0];
+        const int cell = s_cell[j0];
+        cur = tile_box<ORDER, IDEG, BATCH>(P, Q, a, (cell % P.cells_x) * kCellW,
+                                           (cell / P.cells_x) * kCellH, lane, box, &bar[0],
+                                           batch);
       }
-      const FwdPlan& P = batch ? L.plans[s_frame[warp][t]] : p0;
-      HotPlan<IDEG, BATCH> Q;
-      load_hot(P, Q);
-      const Anchor a = s_anc[warp][t];
-      const int local = s_local[warp][t];
-      if (cur.use_box) {
-        if (!mbar_wait(&bar[b], (phase >> b) & 1u)) cur.use_box = false;  // timed out
-        phase ^= 1u << b;
+      for (int t = 0; t < nt; ++t) {
+        const int b = t & 1;
+        TileBox nxt;
+        nxt.use_box = false;
+        if (t + 1 < nt) {
+          const int jn = j0 + (t + 1) / kTilesPerCell, kn = (t + 1) % kTilesPerCell;
+          const FwdPlan& Pn = batch ? L.plans[s_frame[jn]] : p0;
+          HotPlan<IDEG, BATCH> Qn;
+          load_hot(Pn, Qn);
+          const Anchor an = s_anc[jn];
+          const int celln = s_cell[jn];
+          nxt = tile_box<ORDER, IDEG, BATCH>(Pn, Qn, an, (celln % Pn.cells_x) * kCellW,
+                                             (celln / Pn.cells_x) * kCellH + kn * kTileH, lane,
+                                             box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch);
+        }
+        const int j = j0 + t / kTilesPerCell, k = t % kTilesPerCell;
+        const FwdPlan& P = batch ? L.plans[s_frame[j]] : p0;
+        HotPlan<IDEG, BATCH> Q;
+        load_hot(P, Q);
+        const Anchor a = s_anc[j];
+        const int cell = s_cell[j];
+        if (cur.use_box) {
+          if (!mbar_wait(&bar[b], (phase >> b) & 1u)) cur.use_box = false;  // timed out
+          phase ^= 1u << b;
+        }
+        tile_rows<ORDER, IDEG, BATCH>(P, Q, a, (cell % P.cells_x) * kCellW,
+                                      (cell / P.cells_x) * kCellH + k * kTileH, lane,
+                                      box + b * L.box_floats, cur);
+        cur = nxt;
       }
-      tile_rows<ORDER, IDEG, BATCH>(P, Q, a, (local % P.tiles_x) * kTileW, (local / P.tiles_x) * kTileH,
-                             lane, box + b * L.box_floats, cur);
-      cur = nxt;
     }
-    __syncwarp();  // anchors of this chunk are no longer read
     if (!batch) break;
-    int c = 0;
-    if (lane == 0) c = atomicAdd(L.counter, 1);
-    chunk = __shfl_sync(0xffffffffu, c, 0);
+    __syncthreads();  // every warp is done with this unit's anchors
+    if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
+    __syncthreads();
+    unit = s_unit;
   }
 }
 
@@ -580,8 +596,15 @@ static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
 
 const void* forward_kernel(const FwdPlan& p0) { return forward_kernel_for(p0, false); }
 
+// Block size of the kernel that serves this plan.
+static int block_threads(const FwdPlan& p0) {
+  return (p0.flags & DFR_SPLIT) ? kWarps * 32 : kThreads;
+}
+
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s) {
+  (void)threads;
+  threads = block_threads(p0);
   const void* k = forward_kernel_for(p0, L.plans != nullptr);
   if (smem_bytes > 0) {
     // static + dynamic shared memory may exceed the default 48 KB window
@@ -596,6 +619,8 @@ cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int 
 }
 
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes) {
+  (void)threads;
+  threads = block_threads(p0);
   const void* k = forward_kernel_for(p0, true);
   if (smem_bytes > 0)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);

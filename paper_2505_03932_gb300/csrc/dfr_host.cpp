@@ -353,6 +353,8 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   P.h = h;
   P.tiles_x = (w + kTileW - 1) / kTileW;
   P.tiles_y = (h + kTileH - 1) / kTileH;
+  P.cells_x = (w + kCellW - 1) / kCellW;
+  P.cells_y = (h + kCellH - 1) / kCellH;
   P.out = out;
   P.fp = fp;
   P.out_pitch = out_pitch;
@@ -902,9 +904,9 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
   L.box_floats = box_floats(P);
   int grid = L.total_tiles;
   if (flags & DFR_SPLIT) {
-    // one chunk of kChunk tiles per warp
-    const int chunks = (L.total_tiles + kChunk - 1) / kChunk;
-    grid = (chunks + kWarps - 1) / kWarps;
+    // work units of kCellsPerCta anchor cells, one per CTA
+    L.total_tiles = P.cells_x * P.cells_y;
+    grid = (L.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
   }
   // the split kernels leave the coordinate output to a separate kernel (same arithmetic)
   FwdPlan Pk = P;
@@ -945,6 +947,13 @@ bool autotune_enabled() {
   const char* e = std::getenv("DFR_AUTOTUNE");
   return !(e && e[0] == '0');
 }
+
+}  // namespace
+// Work units of one frame in a batched launch: anchor cells (split) or tiles (all-FP64).
+int dfr::batch_units(const FwdPlan& P) {
+  return (P.flags & DFR_SPLIT) ? P.cells_x * P.cells_y : P.tiles_x * P.tiles_y;
+}
+namespace {
 
 // Upload the frame table, zero the work counter and launch the persistent kernel.
 cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int floats, cudaStream_t s) {
@@ -1039,7 +1048,7 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
       return rc;
     }
     c.h_starts[f] = int32_t(total);
-    if (fr.w > 0 && fr.h > 0) total += int64_t(c.h_plans[f].tiles_x) * c.h_plans[f].tiles_y;
+    if (fr.w > 0 && fr.h > 0) total += dfr::batch_units(c.h_plans[f]);
     floats = std::max(floats, box_floats(c.h_plans[f]));
   }
   if (total >= (int64_t(1) << 31)) return fail(DFR_ERR_INVALID_ARG, "batch too large");

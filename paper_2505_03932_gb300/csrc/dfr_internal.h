@@ -18,14 +18,20 @@ constexpr int kMaxCoef = (DFR_MAX_SIP + 1) * (DFR_MAX_SIP + 2) / 2;  // 55
 __host__ __device__ constexpr int poly_off(int p, int n) { return p * (n + 1) - p * (p - 1) / 2; }
 __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) / 2; }
 
-// Target tile (the unit of work of one warp and the anchor cell of the split path): 32 x 8
-// pixels, relative to the bounding-box origin. A warp takes tiles in chunks of kChunk; the
-// chunk's FP64 anchors are computed in parallel, one per lane.
+// Target tile: 32 x 8 pixels, relative to the bounding-box origin; a warp processes a tile at a
+// time (lane = column), with one TMA-staged source box per tile.
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
-constexpr int kChunk = 4;
-constexpr int kWarps = 8;  // warps per CTA of the split forward kernel
+// Anchor cell of the split path: 32 x 32 pixels (four tiles stacked in y), one FP64 anchor at
+// its centre. A CTA of kWarps warps takes kCellsPerCta consecutive cells; their anchors are
+// computed together, one per lane, then each warp processes the tiles of kCellsPerWarp cells.
+constexpr int kCellW = 32;
+constexpr int kCellH = 32;
+constexpr int kTilesPerCell = kCellH / kTileH;
+constexpr int kWarps = 4;
+constexpr int kCellsPerCta = 8;
+constexpr int kCellsPerWarp = kCellsPerCta / kWarps;
 
 // Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
 struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requires
@@ -33,6 +39,7 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   // target bounding box and its tiling
   int32_t x0, y0, w, h;
   int32_t tiles_x, tiles_y;
+  int32_t cells_x, cells_y;
   // outputs (device)
   float* out;
   float* fp;                 // nullable
@@ -75,10 +82,12 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
 // Launch description shared by the forward kernels.
 struct FwdLaunch {
   const FwdPlan* plans;      // batch: device array of n plans (nullptr: single frame in p0)
-  const int32_t* tile_start; // batch: device prefix sums of tiles per frame (n + 1 entries;
-                             // the last is the total tile count)
+  const int32_t* tile_start; // batch: device prefix sums of work units per frame (n + 1
+                             // entries, the last is the total): tiles for the FP64 kernel,
+                             // anchor cells for the split kernel
   int32_t nframes;
-  int32_t total_tiles;       // single frame: tiles in the grid (batch reads tile_start[n])
+  int32_t total_tiles;       // single frame: work units (tiles or cells; batch reads
+                             // tile_start[n])
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
   int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
 };
@@ -122,6 +131,7 @@ int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint3
                    int ideg, FwdPlan& P);
 int inverse_degree_for(const dfr_frame* frames, int n);
 int plan_box_floats(const FwdPlan& P);
+int batch_units(const FwdPlan& P);
 int plan_smem_bytes(int floats);
 int report_error(int code, const char* msg);
 int report_cuda_error(cudaError_t e, const char* where);

@@ -73,7 +73,7 @@ extern "C" int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n,
     if (rc != DFR_OK) return rc;
     g_host_starts[f] = int32_t(total);
     if (frames[f].w > 0 && frames[f].h > 0)
-      total += int64_t(g_host_plans[f].tiles_x) * g_host_plans[f].tiles_y;
+      total += batch_units(g_host_plans[f]);
     floats = std::max(floats, plan_box_floats(g_host_plans[f]));
   }
   if (total >= (int64_t(1) << 31)) return report_error(DFR_ERR_INVALID_ARG, "batch too large");
