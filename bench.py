@@ -183,6 +183,9 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = Clocks(local_rank)
     clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    step()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     times = timed(args.steps, "split")
     wall = time.perf_counter() - t0
