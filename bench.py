@@ -93,6 +93,33 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dfr_fwd.cu", "dfr_device.cuh", "dfr_internal.h"):
+        with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the bench kernel from the committed ncu summary, or None when the
+    kernel source has changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "split_bicubic_4096.md")
+    try:
+        rec = {}
+        for line in open(path):
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch",
+                                                      "kernel_source_sha256"):
+                k, v = line.split(":", 1)
+                rec[k] = v.strip()
+        if rec.get("kernel_source_sha256") == kernel_source_hash():
+            return int(rec["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def workload():
     c = synth.config1()
     return c["src"][0], c["tgt"], c["images"][0]
@@ -235,13 +262,7 @@ def run_gpu(args, rank, world, local_rank):
     peak, peak_src = _peaks()
     achieved = BYTES_PER_PIX * npix / (ms * 1e-3) / 1e9
     value = npix * world / (ms * 1e-3) / 1e6
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("split_bicubic_4096_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = recorded_traffic()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
