@@ -148,7 +148,7 @@ def run_reference(args, rank, world):
         return
     src, tgt, img = workload()
     src = oracle_wcs(src)
-    npix = 40000
+    npix = 1_000_000  # about 1 s of one core per step
     for _ in range(args.warmup):
         oracle_sample_rate(src, tgt, img, npix // 4)
     secs = [oracle_sample_rate(src, tgt, img, npix, seed=100 + k) for k in range(args.steps)]
@@ -267,7 +267,7 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         o_src = oracle_wcs(src_rec)
-        npx = 100000
+        npx = 12_000_000  # about 10 s of one core
         secs = oracle_sample_rate(o_src, tgt_rec, img, npx)
         cpu = {"value": npx / secs / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                "sample": "%d random target pixels of the 4096^2 frame (%.1f s)" % (npx, secs)}
