@@ -30,7 +30,7 @@ constexpr int kCellW = 32;
 constexpr int kCellH = 32;
 constexpr int kTilesPerCell = kCellH / kTileH;
 constexpr int kWarps = 4;
-constexpr int kCellsPerCta = 8;
+constexpr int kCellsPerCta = 4;
 constexpr int kCellsPerWarp = kCellsPerCta / kWarps;
 
 // Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
