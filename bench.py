@@ -301,6 +301,111 @@ def run_gpu(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ other configurations
+def _events_time(fn, k, flush=None):
+    """Median device time (ms, CUDA events around the call) and median host time of the call
+    itself (ms, until it returns)."""
+    import torch
+    ts, hs = [], []
+    for _ in range(k):
+        if flush is not None:
+            flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        t0 = time.perf_counter()
+        fn()
+        hs.append((time.perf_counter() - t0) * 1e3)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), float(np.median(hs))
+
+
+def run_extra(args):
+    """Secondary measurements (not the bench line): the batch configuration (64 uneven frames
+    onto 8192^2, one persistent graph launch vs 64 separate launches), the gradient configuration
+    (2048^2, forward + adjoint) and the stack configuration (32 x 6000x4000 -> 12000x8000,
+    batched forward + per-frame adjoint). One JSON line each."""
+    import torch
+    import paper_2505_03932_gb300 as dfr
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = []
+    if args.workload in ("batch64", "all"):
+        c = synth.config2()
+        tgt = dfr.to_c(c["tgt"])
+        srcs = [dfr.to_c(dfr.fit_inverse_sip(s, 4)[0]) for s in c["src"]]
+        imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
+        bbs = [dfr.target_bbox(s, tgt) for s in srcs]
+        outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
+        fps = [torch.empty_like(o) for o in outs]
+        npx = sum(b[2] * b[3] for b in bbs)
+        dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bilinear", outs=outs, fps=fps)
+        t_batch, h_batch = _events_time(
+            lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bilinear", outs=outs,
+                                        fps=fps), args.steps, flush)
+
+        def separate():
+            for k in range(64):
+                dfr.reproject(imgs[k], srcs[k], tgt, bbox=bbs[k], order="bilinear",
+                              out=outs[k], fp_out=fps[k])
+        separate()
+        t_sep, h_sep = _events_time(separate, args.steps, flush)
+        out.append({"workload": "64 frames (2048-6144 px, SIP3) -> 8192^2, bilinear, split",
+                    "output_mpix": npx / 1e6, "batch_graph_ms": t_batch,
+                    "batch_host_call_ms": h_batch, "separate_launches_ms": t_sep,
+                    "separate_host_calls_ms": h_sep, "batch_mpix_s": npx / t_batch / 1e3,
+                    "separate_mpix_s": npx / t_sep / 1e3,
+                    "roofline_frac_hbm": (12 * npx / (t_batch * 1e-3)) / 1e9 / _peaks()[0]})
+        del imgs, outs, fps
+    if args.workload in ("grad2048", "all"):
+        c = synth.config3()
+        src = dfr.to_c(dfr.fit_inverse_sip(c["src"][0], 4)[0])
+        tgt = dfr.to_c(c["tgt"])
+        img = torch.from_numpy(c["images"][0]).cuda()
+        g = torch.randn((2048, 2048), device="cuda")
+        bb = (0, 0, 2048, 2048)
+        fwd = lambda: dfr.reproject(img, src, tgt, bbox=bb, order="bilinear", exact_inverse=True)
+        bwd = lambda: dfr.reproject_backward(img, src, tgt, g, bb, "bilinear", "split",
+                                             exact_inverse=True)
+        fwd(); bwd()
+        t_f = _events_time(fwd, args.steps, flush)[0]
+        t_b = _events_time(bwd, args.steps, flush)[0]
+        out.append({"workload": "2048^2 SIP3 bilinear, exact inverse, forward + adjoint (split)",
+                    "forward_ms": t_f, "adjoint_ms": t_b,
+                    "forward_mpix_s": 4.194304 / t_f * 1e3, "adjoint_mpix_s": 4.194304 / t_b * 1e3})
+    if args.workload in ("stack32", "all"):
+        c = synth.config4()
+        tgt = dfr.to_c(c["tgt"])
+        srcs = [dfr.to_c(dfr.fit_inverse_sip(s, 6)[0]) for s in c["src"]]
+        imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
+        bbs = [dfr.target_bbox(s, tgt) for s in srcs]
+        outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
+        fps = [torch.empty_like(o) for o in outs]
+        npx = sum(b[2] * b[3] for b in bbs)
+        fwd = lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bicubic", outs=outs, fps=fps)
+        fwd()
+        t_f = _events_time(fwd, max(3, args.steps // 2), flush)[0]
+        gs = [torch.zeros_like(i) for i in imgs]
+        go = torch.randn((max(b[3] for b in bbs), max(b[2] for b in bbs)), device="cuda")
+
+        def bwd():
+            for k in range(32):
+                x0, y0, w, h = bbs[k]
+                dfr.reproject_backward(imgs[k], srcs[k], tgt, go[:h, :w], bbs[k], "bicubic",
+                                       "split", grad_src=gs[k])
+        bwd()
+        t_b = _events_time(bwd, 3, None)[0]
+        out.append({"workload": "32 x 6000x4000 SIP5 -> 12000x8000, bicubic, split batch + adjoint",
+                    "output_mpix": npx / 1e6, "forward_batch_ms": t_f,
+                    "forward_mpix_s": npx / t_f / 1e3, "adjoint_ms": t_b,
+                    "adjoint_mpix_s": npx / t_b / 1e3,
+                    "roofline_frac_hbm": (12 * npx / (t_f * 1e-3)) / 1e9 / _peaks()[0]})
+    for line in out:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,12 +413,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sip3_4096",
+                    choices=["sip3_4096", "batch64", "grad2048", "stack32", "all"],
+                    help="sip3_4096: the bench line; the others print secondary measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "sip3_4096":
+        run_extra(args)
         return
     if world > 1:
         import torch

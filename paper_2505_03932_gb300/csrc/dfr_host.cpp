@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "dfr_internal.h"
@@ -503,7 +504,18 @@ struct DeviceCtx {
   cudaEvent_t done = nullptr;   // recorded after each batched launch (host buffers reusable)
   bool pending = false;
   std::map<GraphKey, cudaGraphExec_t> graphs;
-  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tuned;  // -> (ctas/SM, tma)
+  // batch configuration per (order, flags, degree, log2 n): (1, lanes, -) = graph of
+  // single-frame kernels in `lanes` parallel chains, (0, ctas/SM, tma) = persistent kernel
+  std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> tuned;
+  // fan-out graphs, keyed by the (kernel, grid, smem) signature of their frames
+  // (the source graph stays alive: node updates on the executable graph name its nodes)
+  struct Fan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+    std::vector<FwdPlan> plans;  // parameters each node holds now
+  };
+  std::map<std::vector<uint64_t>, Fan> fans;
 };
 
 std::mutex g_mu;
@@ -542,9 +554,10 @@ int ensure_ctx(DeviceCtx*& out, size_t nframes) {
   return DFR_OK;
 }
 
-// Small cache of built plans: repeated calls with identical arguments (the common case of a
-// pipeline reprojecting into the same buffers) skip the host plan build (box sizing samples
-// the map a few thousand times).
+// Cache of built plans: repeated calls with identical arguments (the common case of a pipeline
+// reprojecting into the same buffers, frame after frame or batch after batch) skip the host plan
+// build (box sizing samples the map a few thousand times; the TMA descriptor is encoded once).
+// Hashed on the key's bytes; the whole cache starts over when it fills.
 struct PlanKey {
   dfr_wcs src, tgt;
   const float* img;
@@ -555,25 +568,39 @@ struct PlanKey {
   int32_t x0, y0, w, h, order;
   uint32_t flags;
   double* coords;
-  int device;
+  int32_t device, ideg;
 };
 
 struct PlanEntry {
   PlanKey key;
   FwdPlan plan;
-  uint64_t used;
 };
 
 std::mutex g_plan_mu;
 std::vector<PlanEntry> g_plans;
-uint64_t g_plan_clock = 0;
-constexpr size_t kPlanCacheSize = 8;
+std::unordered_multimap<uint64_t, size_t> g_plan_index;
+constexpr size_t kPlanCacheSize = 256;
+
+uint64_t key_hash(const PlanKey& k) {
+  // 64-bit multiply-xorshift over the key's words
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(&k);
+  uint64_t h = 0x9e3779b97f4a7c15ull ^ sizeof(k);
+  size_t i = 0;
+  for (; i + 8 <= sizeof(k); i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b + i, 8);
+    h = (h ^ w) * 0xff51afd7ed558ccdull;
+    h ^= h >> 32;
+  }
+  for (; i < sizeof(k); ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+  return h;
+}
 
 int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
                 float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
-                int32_t h, int32_t order, uint32_t flags, double* coords, FwdPlan& P) {
+                int32_t h, int32_t order, uint32_t flags, double* coords, int ideg, FwdPlan& P) {
   if (!src || !tgt) return build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h,
-                                      order, flags, coords, -1, P);
+                                      order, flags, coords, ideg, P);
   PlanKey k;
   std::memset(&k, 0, sizeof(k));
   k.src = *src;
@@ -590,27 +617,28 @@ int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_
   k.order = order;
   k.flags = flags;
   k.coords = coords;
+  k.ideg = ideg;
   if (cudaGetDevice(&k.device) != cudaSuccess) k.device = -1;
+  const uint64_t hk = key_hash(k);
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
-    for (PlanEntry& e : g_plans)
-      if (std::memcmp(&e.key, &k, sizeof(k)) == 0) {
-        e.used = ++g_plan_clock;
-        P = e.plan;
+    auto range = g_plan_index.equal_range(hk);
+    for (auto it = range.first; it != range.second; ++it)
+      if (std::memcmp(&g_plans[it->second].key, &k, sizeof(k)) == 0) {
+        P = g_plans[it->second].plan;
         return DFR_OK;
       }
   }
   int rc = build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h, order, flags,
-                      coords, -1, P);
+                      coords, ideg, P);
   if (rc != DFR_OK) return rc;
   std::lock_guard<std::mutex> lock(g_plan_mu);
-  if (g_plans.size() < kPlanCacheSize) {
-    g_plans.push_back(PlanEntry{k, P, ++g_plan_clock});
-  } else {
-    auto lru = std::min_element(g_plans.begin(), g_plans.end(),
-                                [](const PlanEntry& a, const PlanEntry& b) { return a.used < b.used; });
-    *lru = PlanEntry{k, P, ++g_plan_clock};
+  if (g_plans.size() >= kPlanCacheSize) {
+    g_plans.clear();
+    g_plan_index.clear();
   }
+  g_plans.push_back(PlanEntry{k, P});
+  g_plan_index.emplace(hk, g_plans.size() - 1);
   return DFR_OK;
 }
 
@@ -896,7 +924,7 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
                   double* coords_out, void* stream) {
   FwdPlan P;
   int rc = cached_plan(src, tgt, src_img, src_pitch, out, footprint, out_pitch, x0, y0, out_w,
-                       out_h, order, flags, coords_out, P);
+                       out_h, order, flags, coords_out, -1, P);
   if (rc != DFR_OK) return rc;
   if (out_w == 0 || out_h == 0) return DFR_OK;
   FwdLaunch L{};
@@ -975,9 +1003,127 @@ cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int floats, cudaStream_
                         smem_for_floats(floats), s);
 }
 
-// Tile-launch autotuner: CTAs per SM of the persistent grid and TMA staging on/off, timed on
-// the caller's data (outputs are rewritten identically by every candidate).
-std::pair<int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStream_t s) {
+// Fan-out form of a batch: one single-frame kernel per frame as independent nodes of one CUDA
+// graph (the frames run concurrently); node parameters are rewritten on every call, so the
+// graph is rebuilt only when a frame's kernel, grid or shared memory changes.
+struct FanItem {
+  const void* func;
+  int grid, threads, smem;
+  FwdPlan plan;
+  FwdLaunch launch;
+};
+
+int fan_items(const DeviceCtx& c, int n, std::vector<FanItem>& items) {
+  items.clear();
+  for (int f = 0; f < n; ++f) {
+    const FwdPlan& P = c.h_plans[f];
+    if (P.w <= 0 || P.h <= 0) continue;
+    FanItem it;
+    it.plan = P;
+    std::memset(&it.launch, 0, sizeof(it.launch));
+    it.launch.box_floats = box_floats(P);
+    it.func = forward_kernel(P);
+    it.smem = smem_for(P);
+    if (P.flags & DFR_SPLIT) {
+      it.launch.total_tiles = P.cells_x * P.cells_y;
+      it.grid = (it.launch.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
+      it.threads = kWarps * 32;
+    } else {
+      it.launch.total_tiles = P.tiles_x * P.tiles_y;
+      it.grid = it.launch.total_tiles;
+      it.threads = forward_threads_default();
+    }
+    items.push_back(it);
+  }
+  // each kernel's dynamic shared-memory limit must cover the largest of its nodes
+  std::map<const void*, int> need;
+  for (const FanItem& it : items) need[it.func] = std::max(need[it.func], it.smem);
+  for (const auto& kv : need) {
+    if (kv.second <= 0) continue;
+    cudaError_t e = cudaFuncSetAttribute(kv.first, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kv.second);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  return DFR_OK;
+}
+
+int launch_fan(DeviceCtx& c, int n, int lanes, cudaStream_t s) {
+  std::vector<FanItem> items;
+  int rc = fan_items(c, n, items);
+  if (rc != DFR_OK) return rc;
+  if (items.empty()) return DFR_OK;
+  lanes = std::max(1, lanes);
+  std::vector<uint64_t> key{uint64_t(lanes)};
+  for (const FanItem& it : items) {
+    key.push_back(reinterpret_cast<uint64_t>(it.func));
+    key.push_back((uint64_t(uint32_t(it.grid)) << 32) | uint32_t(it.smem));
+  }
+  auto params = [](FanItem& it, void** args) {
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void*>(it.func);
+    kp.gridDim = dim3(it.grid);
+    kp.blockDim = dim3(it.threads);
+    kp.sharedMemBytes = unsigned(it.smem);
+    args[0] = &it.plan;
+    args[1] = &it.launch;
+    kp.kernelParams = args;
+    return kp;
+  };
+  auto f = c.fans.find(key);
+  if (f == c.fans.end()) {
+    if (c.fans.size() >= 16) {  // bound the cache: many distinct frame mixes start it over
+      DFR_CUDA(cudaStreamSynchronize(s));
+      for (auto& kv : c.fans) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+      }
+      c.fans.clear();
+    }
+    cudaGraph_t graph = nullptr;
+    DFR_CUDA(cudaGraphCreate(&graph, 0));
+    DeviceCtx::Fan fan;
+    for (size_t i = 0; i < items.size(); ++i) {
+      void* args[2];
+      cudaKernelNodeParams kp = params(items[i], args);
+      cudaGraphNode_t node;
+      // node i follows node i - lanes: `lanes` chains of frames run side by side
+      const bool dep = i >= size_t(lanes);
+      cudaError_t e = cudaGraphAddKernelNode(&node, graph, dep ? &fan.nodes[i - lanes] : nullptr,
+                                             dep ? 1 : 0, &kp);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "cudaGraphAddKernelNode");
+      }
+      fan.nodes.push_back(node);
+      fan.plans.push_back(items[i].plan);
+    }
+    cudaError_t e = cudaGraphInstantiate(&fan.exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(e, "cudaGraphInstantiate (fan-out)");
+    }
+    fan.graph = graph;
+    f = c.fans.emplace(key, fan).first;
+  } else {
+    // the launch parameters follow from the plan and the key; update changed nodes only
+    for (size_t i = 0; i < items.size(); ++i) {
+      if (std::memcmp(&f->second.plans[i], &items[i].plan, sizeof(FwdPlan)) == 0) continue;
+      void* args[2];
+      cudaKernelNodeParams kp = params(items[i], args);
+      DFR_CUDA(cudaGraphExecKernelNodeSetParams(f->second.exec, f->second.nodes[i], &kp));
+      f->second.plans[i] = items[i].plan;
+    }
+  }
+  DFR_CUDA(cudaGraphLaunch(f->second.exec, s));
+  return DFR_OK;
+}
+
+// Batch autotuner, timed on the caller's data (outputs are rewritten identically by every
+// candidate): graphs of single-frame kernels in 1, 2, 4 or up to 64 parallel chains, and the
+// persistent kernel with several CTAs per SM, with and without TMA staging. Returns the
+// configuration tuple kept in DeviceCtx::tuned.
+std::tuple<int, int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStream_t s) {
   const int threads = forward_threads_default();
   const int smem = smem_for_floats(floats);
   const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
@@ -994,7 +1140,23 @@ std::pair<int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStr
   cudaEventCreate(&e1);
   std::vector<FwdPlan> saved(c.h_plans, c.h_plans + n);
   float best = 1e30f;
-  std::pair<int, int> pick = cand.empty() ? std::make_pair(1, 0) : cand[0];
+  std::tuple<int, int, int> pick = std::make_tuple(1, 1, 1);
+  for (int lanes : {1, 2, 4, 64}) {
+    // graphs of single-frame kernels in `lanes` parallel chains
+    if (lanes > 1 && lanes / 2 >= n) break;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s);
+      ok = launch_fan(c, n, lanes, s) == DFR_OK;
+    }
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      pick = std::make_tuple(1, lanes, 1);
+    }
+  }
   for (auto cd : cand) {
     for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = cd.second ? saved[f].use_tma : 0;
     const int fl = cd.second ? floats : 0;
@@ -1010,7 +1172,7 @@ std::pair<int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStr
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      pick = cd;
+      pick = std::make_tuple(0, cd.first, cd.second);
     }
   }
   std::copy(saved.begin(), saved.end(), c.h_plans);
@@ -1041,8 +1203,8 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   int floats = 0;
   for (int f = 0; f < n; ++f) {
     const dfr_frame& fr = frames[f];
-    rc = build_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
-                    fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, c.h_plans[f]);
+    rc = cached_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
+                     fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, c.h_plans[f]);
     if (rc != DFR_OK) {
       g_err = "frame " + std::to_string(f) + ": " + g_err;
       return rc;
@@ -1057,22 +1219,24 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
 
   const auto tkey = std::make_tuple(order, int(flags), ideg, 31 - __builtin_clz(unsigned(n)));
   auto it = c.tuned.find(tkey);
-  std::pair<int, int> cfg;
+  std::tuple<int, int, int> cfg;
   if (it != c.tuned.end()) {
     cfg = it->second;
   } else if (autotune_enabled()) {
     cfg = autotune(c, n, floats, int(total), s);
     c.tuned[tkey] = cfg;
   } else {
-    cfg = {std::min(4, forward_max_blocks_per_sm(c.h_plans[0], forward_threads_default(),
-                                                 smem_for_floats(floats))),
-           floats > 0 ? 1 : 0};
+    cfg = std::make_tuple(1, 1, 1);  // one chain of single-frame kernels
   }
-  if (!cfg.second) {
+  if (std::get<0>(cfg) == 1) {
+    // kernel parameters are copied into the graph: nothing host-side to protect afterwards
+    return launch_fan(c, n, std::get<1>(cfg), s);
+  }
+  if (!std::get<2>(cfg)) {
     for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = 0;
     floats = 0;
   }
-  const int grid = std::max(1, std::min(int(total), c.sms * cfg.first));
+  const int grid = std::max(1, std::min(int(total), c.sms * std::get<1>(cfg)));
   GraphKey gk{n, order, int(flags), ideg, grid, floats, 0};
   auto g = c.graphs.find(gk);
   if (g == c.graphs.end()) {
