@@ -96,7 +96,7 @@ class Clocks:
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("dfr_fwd.cu", "dfr_device.cuh", "dfr_internal.h"):
+    for f in ("dfr_fwd.cu", "dfr_tile.cuh", "dfr_device.cuh", "dfr_internal.h"):
         with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -402,6 +402,31 @@ def run_extra(args):
                     "forward_mpix_s": npx / t_f / 1e3, "adjoint_ms": t_b,
                     "adjoint_mpix_s": npx / t_b / 1e3,
                     "roofline_frac_hbm": (12 * npx / (t_f * 1e-3)) / 1e9 / _peaks()[0]})
+    if args.workload in ("adjoint6000", "all"):
+        # one 6000x4000 SIP5 exposure of the stack configuration: forward, adjoint with the
+        # polynomial inverse (CRVAL and CD gradients), adjoint with the Newton inverse (A/B too)
+        c = synth.config4(n_frames=1)
+        tgt = dfr.to_c(c["tgt"])
+        src = dfr.to_c(dfr.fit_inverse_sip(c["src"][0], 6)[0])
+        img = torch.from_numpy(c["images"][0]).cuda()
+        bb = dfr.target_bbox(src, tgt)
+        npx = bb[2] * bb[3]
+        go = torch.randn((bb[3], bb[2]), device="cuda")
+        gs = torch.zeros_like(img)
+        fwd = lambda: dfr.reproject(img, src, tgt, bbox=bb, order="bicubic")
+        bwd = lambda: dfr.reproject_backward(img, src, tgt, go, bb, "bicubic", "split",
+                                             grad_src=gs)
+        bwx = lambda: dfr.reproject_backward(img, src, tgt, go, bb, "bicubic", "split",
+                                             exact_inverse=True, grad_src=gs)
+        fwd(); bwd(); bwx()
+        t_f = _events_time(fwd, args.steps, flush)[0]
+        t_b = _events_time(bwd, args.steps, flush)[0]
+        t_x = _events_time(bwx, args.steps, flush)[0]
+        out.append({"workload": "6000x4000 SIP5 (AP/BP 6) -> stack target, bicubic, split",
+                    "output_mpix": npx / 1e6, "forward_ms": t_f, "adjoint_ms": t_b,
+                    "adjoint_exact_ms": t_x, "forward_mpix_s": npx / t_f / 1e3,
+                    "adjoint_mpix_s": npx / t_b / 1e3, "adjoint_exact_mpix_s": npx / t_x / 1e3,
+                    "adjoint_roofline_frac_hbm": (12 * npx / (t_b * 1e-3)) / 1e9 / _peaks()[0]})
     for line in out:
         print(json.dumps(line), flush=True)
 
@@ -414,7 +439,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sip3_4096",
-                    choices=["sip3_4096", "batch64", "grad2048", "stack32", "all"],
+                    choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "all"],
                     help="sip3_4096: the bench line; the others print secondary measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -303,8 +303,10 @@ def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=Non
 
 def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinear",
                        precision="split", exact_inverse=False, grad_src=None, want_src=True,
-                       want_params=True, stream=None):
-    """Adjoint of reproject (dfr_reproject_backward): returns (grad_src, grad_params)."""
+                       want_params=True, stream=None, tma=True):
+    """Adjoint of reproject (dfr_reproject_backward): returns (grad_src, grad_params).
+
+    ``tma=False`` selects the per-pixel kernel (no staged source / gradient boxes)."""
     torch = _torch()
     src_img = _dev_f32(src_img, "src_img")
     grad_out = _dev_f32(grad_out, "grad_out")
@@ -319,7 +321,7 @@ def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinea
         ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)),
         ctypes.c_void_p(src_img.data_ptr()), src_img.stride(0),
         ctypes.c_void_p(grad_out.data_ptr()), grad_out.stride(0), x0, y0, w, h, _order(order),
-        _flags(precision, exact_inverse, True),
+        _flags(precision, exact_inverse, tma),
         ctypes.c_void_p(gs.data_ptr() if gs is not None else 0), gs.stride(0) if gs is not None else 0,
         ctypes.c_void_p(gp.data_ptr() if gp is not None else 0), _stream_ptr(stream)))
     return gs, gp

@@ -10,16 +10,16 @@
 // them with shuffles and adds the warp total to an FP64 shared accumulator; each CTA writes
 // one FP64 partial per parameter and a final single-block kernel adds the partials in a fixed
 // order (deterministic parameter gradients).
+//
+// This file holds the per-pixel kernel (FP64 path, and split plans the tile-staged kernel of
+// dfr_bwd_tile.cu does not serve), the final sum and the dispatch between the two.
 #include <climits>
 
-#include "dfr_device.cuh"
+#include "dfr_adjoint.cuh"
 
 namespace dfr {
 
 constexpr int kBwdThreads = 256;
-constexpr float kR0f = 57.29577951308232f;
-
-__host__ __device__ constexpr int nterms(int fd) { return fd > 0 ? (fd + 1) * (fd + 2) / 2 - 1 : 0; }
 
 // FP64 geometry of one target pixel: source position, intermediate offsets before (U, V) and
 // after (u, v) the inverse SIP. Same arithmetic as the forward FP64 path.
@@ -49,12 +49,6 @@ __device__ __forceinline__ bool fp64_geo(const FwdPlan& P, double X, double Y, d
   return ok;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <int ORDER, int FD>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant__ FwdPlan P,
                                                           const __grid_constant__ BwdExtra B) {
@@ -70,12 +64,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
   const bool exact = (P.flags & DFR_EXACT_INVERSE) && P.fsip_deg > 0;
   const bool want_params = B.grad_params != nullptr && ORDER != DFR_NEAREST;
   const int ntiles = P.tiles_x * P.tiles_y;
-  // CD, CD^-1 and the tangent point in FP32 for the per-pixel chain rule
-  const float cd00 = float(P.cd_s[0][0]), cd01 = float(P.cd_s[0][1]);
-  const float cd10 = float(P.cd_s[1][0]), cd11 = float(P.cd_s[1][1]);
-  const float ci00 = float(P.cdinv_s[0][0]), ci01 = float(P.cdinv_s[0][1]);
-  const float ci10 = float(P.cdinv_s[1][0]), ci11 = float(P.cdinv_s[1][1]);
-  const float sd0 = float(P.sd0_s), cd0 = float(P.cd0_s);
+  const ChainConst K = chain_const(P);
   __syncthreads();
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -199,43 +188,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
         }
       }
       if (!want_params) continue;  // uniform over the launch
-      // chain rule: (gxs, gys) -> lambda = dL/d(U, V)
-      float m00 = 1.f, m01 = 0.f, m10 = 0.f, m11 = 1.f;
-      if (cov) {
-        if (exact) {
-          float A, Au, Av, Bq, Bu, Bv;
-          horner_grad_rt<float>(P.fsip_f[0], P.fsip_deg, u, v, A, Au, Av);
-          horner_grad_rt<float>(P.fsip_f[1], P.fsip_deg, u, v, Bq, Bu, Bv);
-          const float j00 = 1.f + Au, j01 = Av, j10 = Bu, j11 = 1.f + Bv;
-          const float inv = __fdividef(1.f, fmaf(j00, j11, -j01 * j10));
-          m00 = j11 * inv;
-          m01 = -j01 * inv;
-          m10 = -j10 * inv;
-          m11 = j00 * inv;
-        } else if (P.isip_deg > 0) {
-          float A, Au, Av, Bq, Bu, Bv;
-          horner_grad_rt<float>(P.isip_f[0], P.isip_deg, U, V, A, Au, Av);
-          horner_grad_rt<float>(P.isip_f[1], P.isip_deg, U, V, Bq, Bu, Bv);
-          m00 = 1.f + Au;
-          m01 = Av;
-          m10 = Bu;
-          m11 = 1.f + Bv;
-        }
-      }
-      const float lu = fmaf(gxs, m00, gys * m10);
-      const float lv = fmaf(gxs, m01, gys * m11);
-      // nu = CD^-T lambda = dL/d(u', v') (degrees)
-      const float nx = fmaf(ci00, lu, ci10 * lv);
-      const float ny = fmaf(ci01, lu, ci11 * lv);
-      const float xi = fmaf(cd00, U, cd01 * V) / kR0f;
-      const float eta = fmaf(cd10, U, cd11 * V) / kR0f;
-      float c[6];
-      c[0] = nx * fmaf(-cd0, fmaf(xi, xi, 1.f), sd0 * eta) + ny * (-xi * fmaf(cd0, eta, sd0));
-      c[1] = nx * (-xi * eta) + ny * (-fmaf(eta, eta, 1.f));
-      c[2] = -nx * U;
-      c[3] = -nx * V;
-      c[4] = -ny * U;
-      c[5] = -ny * V;
+      float lu, lv, c[6];
+      chain_terms<-1, -1>(P, K, cov, exact, gxs, gys, U, V, u, v, lu, lv, c);
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
         const float t = warp_sum(c[q]);
@@ -290,7 +244,6 @@ __global__ void bwd_finalize(const __grid_constant__ BwdExtra B, int np) {
 }
 
 int backward_num_padded(int fd) { return 6 + 2 * nterms(fd); }
-int backward_threads() { return kBwdThreads; }
 
 template <int ORDER>
 static const void* bwd_for_order(int fd) {
@@ -302,7 +255,15 @@ static const void* bwd_for_order(int fd) {
   }
 }
 
+// The tile-staged kernel serves split-precision plans with a TMA-capable source and exact-inverse
+// degree <= 5 (its per-lane accumulators: 6 + 2 * 20 registers); the per-pixel kernel serves
+// the rest (FP64 path, degree 9, sources without a tensor map).
+static bool staged(const FwdPlan& p0, int fd) {
+  return (p0.flags & DFR_SPLIT) && p0.use_tma && fd <= 5;
+}
+
 static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
+  if (staged(p0, fd)) return backward_tile_kernel(p0.order, p0.isip_deg, fd);
   switch (p0.order) {
     case DFR_NEAREST: return bwd_for_order<DFR_NEAREST>(fd);
     case DFR_BILINEAR: return bwd_for_order<DFR_BILINEAR>(fd);
@@ -310,10 +271,22 @@ static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
   }
 }
 
-int backward_max_blocks_per_sm(const FwdPlan& p0, int fd) {
+int backward_threads_for(const FwdPlan& p0, int fd) {
+  return staged(p0, fd) ? kWarps * 32 : kBwdThreads;
+}
+
+// Dynamic shared memory: per warp a source box and a gradient box, plus alignment slack.
+int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats) {
+  return staged(p0, fd) ? kWarps * 2 * box_floats * 4 + 128 : 0;
+}
+
+int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes) {
+  const void* k = bwd_kernel_for(p0, fd);
+  if (smem_bytes > 0)
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwd_kernel_for(p0, fd), kBwdThreads,
-                                                    0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, backward_threads_for(p0, fd),
+                                                    size_t(smem_bytes)) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
@@ -322,8 +295,14 @@ cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s
   FwdPlan p = p0;
   BwdExtra b = B;
   void* args[] = {&p, &b};
-  cudaError_t e = cudaLaunchKernel(bwd_kernel_for(p0, B.fd), dim3(B.grid), dim3(kBwdThreads),
-                                   args, 0, s);
+  const void* k = bwd_kernel_for(p0, B.fd);
+  const int smem = backward_smem_bytes(p0, B.fd, B.box_floats);
+  if (smem > 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaLaunchKernel(k, dim3(B.grid), dim3(backward_threads_for(p0, B.fd)), args,
+                                   size_t(smem), s);
   if (e != cudaSuccess || B.grad_params == nullptr) return e;
   int np = backward_num_padded(B.fd);
   void* fargs[] = {&b, &np};

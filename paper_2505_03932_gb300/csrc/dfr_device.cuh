@@ -82,6 +82,29 @@ __device__ __forceinline__ void horner_pair_rt(const T* ca, const T* cb, int n, 
 }
 
 // Value and first partials of one polynomial (runtime degree): P, dP/du, dP/dv.
+// Compile-time-degree form of horner_grad_rt below: the same FMA sequence, unrolled, so both
+// give equal bits for the same (zero-padded) coefficients.
+template <int N, typename T>
+__device__ __forceinline__ void horner_grad(const T* c, T u, T v, T& P, T& Pu, T& Pv) {
+  T p_ = T(0), pu = T(0), pv = T(0);
+#pragma unroll
+  for (int p = N; p >= 0; --p) {
+    const int off = poly_off(p, N);
+    T q_ = c[off + (N - p)], qv = T(0);
+#pragma unroll
+    for (int q = N - p - 1; q >= 0; --q) {
+      qv = fma(qv, v, q_);
+      q_ = fma(q_, v, c[off + q]);
+    }
+    pu = fma(pu, u, p_);
+    p_ = fma(p_, u, q_);
+    pv = fma(pv, u, qv);
+  }
+  P = p_;
+  Pu = pu;
+  Pv = pv;
+}
+
 template <typename T>
 __device__ __forceinline__ void horner_grad_rt(const T* c, int n, T u, T v, T& P, T& Pu, T& Pv) {
   T p_ = T(0), pu = T(0), pv = T(0);
@@ -99,6 +122,16 @@ __device__ __forceinline__ void horner_grad_rt(const T* c, int n, T u, T v, T& P
   P = p_;
   Pu = pu;
   Pv = pv;
+}
+
+// Value and gradient of a packed polynomial of degree DEG (> 0: compile time; < 0: the runtime
+// degree n). Both forms give equal bits.
+template <int DEG, typename T>
+__device__ __forceinline__ void poly_grad(const T* c, int n, T u, T v, T& P, T& Pu, T& Pv) {
+  if (DEG > 0)
+    horner_grad<(DEG > 0 ? DEG : 1), T>(c, u, v, P, Pu, Pv);
+  else
+    horner_grad_rt<T>(c, n, u, v, P, Pu, Pv);
 }
 
 // ---------------------------------------------------------------- interpolation weights
@@ -354,9 +387,11 @@ __device__ __forceinline__ int cell_anchor_y(const FwdPlan& P, int gy) {
 // of that degree over cab, which may live in registers; IDEG > 0 without PAIRS: the same in
 // scalar FMAs over the plan's arrays; IDEG < 0: runtime degree P.isip_deg over the plan's
 // arrays; IDEG == 0: no inverse polynomial). All forms run the same FMA sequence, so they
-// give the same bits. The rarely used target-SIP and Newton branches read the plan P.
+// give the same bits. The rarely used target-SIP and Newton branches read the plan P; the
+// Newton step's forward SIP has degree FDEG (the plan's padded degree) or, with FDEG < 0, the
+// runtime degree.
 // geo (nullable) receives (du, dv, eu, ev) for the adjoint.
-template <int IDEG, bool PAIRS = true>
+template <int IDEG, bool PAIRS = true, int FDEG = -1>
 __device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2* cab,
                                                   bool identity, bool tsip, bool newton,
                                                   const Anchor& a, float dx, float dy, float& xr,
@@ -404,8 +439,8 @@ __device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2
     // Newton on e = u - U0: e + A(U0 + e) = du, started from the AP/BP estimate.
     for (int it = 0; it < P.newton_iters; ++it) {
       float A, Au, Av, B, Bu, Bv;
-      horner_grad_rt<float>(P.fsip_f[0], P.fsip_deg, a.U0 + eu, a.V0 + ev, A, Au, Av);
-      horner_grad_rt<float>(P.fsip_f[1], P.fsip_deg, a.U0 + eu, a.V0 + ev, B, Bu, Bv);
+      poly_grad<FDEG, float>(P.fsip_f[0], P.fsip_deg, a.U0 + eu, a.V0 + ev, A, Au, Av);
+      poly_grad<FDEG, float>(P.fsip_f[1], P.fsip_deg, a.U0 + eu, a.V0 + ev, B, Bu, Bv);
       const float ru = (eu - du) + A, rv = (ev - dv) + B;
       const float j00 = 1.f + Au, j11 = 1.f + Bv;
       const float det = fmaf(j00, j11, -Av * Bu);

@@ -169,6 +169,15 @@ int sip_round_degree(int order) {
   return 9;
 }
 
+// Degree the forward A/B polynomials are packed at for the Newton inverse and the adjoint's
+// parameter layout (zero-padded: Horner gives equal bits, and kernels specialise on it).
+int forward_round_degree(int order) {
+  if (order <= 0) return 0;
+  if (order <= 3) return 3;
+  if (order <= 5) return 5;
+  return 9;
+}
+
 template <typename T>
 void pack_poly(const double c[10][10], int order, int deg, T* out) {
   for (int k = 0; k < kMaxCoef; ++k) out[k] = T(0);
@@ -387,7 +396,7 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   pack_poly(src->bp, src->bp_order, P.isip_deg, P.isip_d[1]);
   pack_poly(src->ap, src->ap_order, P.isip_deg, P.isip_f[0]);
   pack_poly(src->bp, src->bp_order, P.isip_deg, P.isip_f[1]);
-  P.fsip_deg = exact ? std::max(src->a_order, src->b_order) : 0;
+  P.fsip_deg = exact ? forward_round_degree(std::max(src->a_order, src->b_order)) : 0;
   pack_poly(src->a, src->a_order, std::max(P.fsip_deg, 0), P.fsip_d[0]);
   pack_poly(src->b, src->b_order, std::max(P.fsip_deg, 0), P.fsip_d[1]);
   pack_poly(src->a, src->a_order, std::max(P.fsip_deg, 0), P.fsip_f[0]);
@@ -1269,12 +1278,6 @@ struct BwdScratch {
 };
 std::map<int, BwdScratch> g_bwd;
 
-int padded_fd(int order) {
-  if (order <= 0) return 0;
-  if (order <= 3) return 3;
-  if (order <= 5) return 5;
-  return 9;
-}
 
 }  // namespace
 }  // namespace dfr
@@ -1286,10 +1289,12 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       uint32_t flags, float* grad_src, int64_t gs_pitch,
                                       double* grad_params, void* stream) {
   FwdPlan P;
-  // the forward plan (outputs unused) gives the same source positions as dfr_reproject
+  // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
+  // split path stages source and gradient boxes by tile, as sized by the plan
   float* dummy = reinterpret_cast<float*>(uintptr_t(16));
-  int rc = build_plan(src, tgt, src_img, src_pitch, dummy, nullptr, out_w, x0, y0, out_w, out_h,
-                      order, flags | DFR_NO_TMA, nullptr, -1, P);
+  const uint32_t pflags = (flags & DFR_SPLIT) ? flags : (flags | DFR_NO_TMA);
+  int rc = cached_plan(src, tgt, src_img, src_pitch, dummy, nullptr, out_w, x0, y0, out_w, out_h,
+                       order, pflags, nullptr, -1, P);
   if (rc != DFR_OK) return rc;
   if (out_w > 0 && out_h > 0) {
     if (!grad_out) return fail(DFR_ERR_INVALID_ARG, "grad_out must be non-NULL");
@@ -1307,7 +1312,7 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   B.grad_params = grad_params;
   B.nout = dfr_num_params(src);
   const bool exact = (flags & DFR_EXACT_INVERSE) && (src->a_order > 0 || src->b_order > 0);
-  B.fd = exact ? padded_fd(std::max(src->a_order, src->b_order)) : 0;
+  B.fd = exact ? forward_round_degree(std::max(src->a_order, src->b_order)) : 0;
   // padded layout -> public layout
   const int np = backward_num_padded(B.fd);
   for (int k = 0; k < kMaxParams; ++k) B.pmap[k] = -1;
@@ -1336,9 +1341,18 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   DFR_CUDA(cudaGetDevice(&dev));
   BwdScratch& S = g_bwd[dev];
   if (S.sms == 0) DFR_CUDA(cudaDeviceGetAttribute(&S.sms, cudaDevAttrMultiProcessorCount, dev));
-  const int ntiles = P.tiles_x * P.tiles_y;
-  const int per_sm = std::min(4, backward_max_blocks_per_sm(P, B.fd));
-  B.grid = std::max(1, std::min(ntiles, S.sms * per_sm));
+  B.box_floats = box_floats(P);
+  const int smem = backward_smem_bytes(P, B.fd, B.box_floats);
+  if (smem > 0) {
+    // tile-staged kernel: CTAs resident at once stride over units of kCellsPerCta cells
+    const int units = (P.cells_x * P.cells_y + kCellsPerCta - 1) / kCellsPerCta;
+    const int per_sm = backward_max_blocks_per_sm(P, B.fd, smem);
+    B.grid = std::max(1, std::min(units, S.sms * per_sm));
+  } else {
+    const int ntiles = P.tiles_x * P.tiles_y;
+    const int per_sm = std::min(4, backward_max_blocks_per_sm(P, B.fd, 0));
+    B.grid = std::max(1, std::min(ntiles, S.sms * per_sm));
+  }
   if (grad_params) {
     const size_t need = size_t(B.grid) * size_t(np);
     if (need > S.cap) {

@@ -106,6 +106,7 @@ struct BwdExtra {
   int32_t nout;              // dfr_num_params(src)
   int32_t fd;                // padded A/B degree of the parameter layout (0: A/B not live)
   int32_t grid;
+  int32_t box_floats;        // split path: floats of each warp's source / gradient box (0: none)
   int16_t pmap[kMaxParams];
 };
 
@@ -123,8 +124,10 @@ cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
-int backward_max_blocks_per_sm(const FwdPlan& p0, int fd);
-int backward_threads();
+int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
+int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats);
+int backward_threads_for(const FwdPlan& p0, int fd);
+const void* backward_tile_kernel(int order, int ideg, int fd);  // dfr_bwd_tile.cu
 
 // Plan-builder access for translation units other than dfr_host.cpp.
 int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint32_t flags,
