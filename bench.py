@@ -96,7 +96,8 @@ class Clocks:
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("dfr_fwd.cu", "dfr_tile.cuh", "dfr_device.cuh", "dfr_internal.h"):
+    for f in ("dfr_fwd.cu", "dfr_fwd_kernels.cuh", "dfr_tile.cuh", "dfr_device.cuh",
+              "dfr_internal.h"):
         with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -427,6 +428,34 @@ def run_extra(args):
                     "adjoint_exact_ms": t_x, "forward_mpix_s": npx / t_f / 1e3,
                     "adjoint_mpix_s": npx / t_b / 1e3, "adjoint_exact_mpix_s": npx / t_x / 1e3,
                     "adjoint_roofline_frac_hbm": (12 * npx / (t_b * 1e-3)) / 1e9 / _peaks()[0]})
+    if args.workload in ("coadd32", "all"):
+        # the stack configuration co-added onto its 12000x8000 target, then normalised
+        c = synth.config4()
+        tgt = dfr.to_c(c["tgt"])
+        srcs = [dfr.to_c(dfr.fit_inverse_sip(s, 6)[0]) for s in c["src"]]
+        imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
+        bbs = [dfr.target_bbox(s, tgt) for s in srcs]
+        npx = sum(b[2] * b[3] for b in bbs)
+        NX, NY = int(tgt.naxis[0]), int(tgt.naxis[1])
+        sv = torch.zeros((NY, NX), device="cuda")
+        sf = torch.zeros_like(sv)
+        mean = torch.empty_like(sv)
+
+        def co():
+            sv.zero_()
+            sf.zero_()
+            dfr.coadd(imgs, srcs, tgt, bboxes=bbs, order="bicubic", sum_vf=sv, sum_f=sf)
+        co()
+        t_c = _events_time(co, max(3, args.steps // 2), flush)[0]
+        t_z = _events_time(lambda: (sv.zero_(), sf.zero_()), 5, flush)[0]
+        nz = lambda: dfr.coadd_normalize(sv, sf, out=mean)
+        nz()
+        t_n = _events_time(nz, args.steps, flush)[0]
+        out.append({"workload": "co-add of 32 x 6000x4000 SIP5 onto 12000x8000, bicubic, split",
+                    "frame_mpix": npx / 1e6, "coadd_ms": t_c - t_z, "zero_sums_ms": t_z,
+                    "coadd_frame_mpix_s": npx / (t_c - t_z) / 1e3, "normalize_ms": t_n,
+                    "normalize_roofline_frac_hbm":
+                        (12 * NX * NY / (t_n * 1e-3)) / 1e9 / _peaks()[0]})
     for line in out:
         print(json.dumps(line), flush=True)
 
@@ -439,7 +468,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sip3_4096",
-                    choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "all"],
+                    choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "coadd32",
+                             "all"],
                     help="sip3_4096: the bench line; the others print secondary measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

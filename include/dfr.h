@@ -125,13 +125,14 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
                   int32_t x0, int32_t y0, int32_t out_w, int32_t out_h,
                   int32_t order, uint32_t flags, double* coords_out, void* stream);
 
-/* Reproject n exposures onto one target grid in a single persistent launch (the paper's
- * pipeline stacks >1000 exposures, Sec. 2). Every frame's pixels are computed with exactly
- * the arithmetic of dfr_reproject for the same bounding box and flags, so results are equal
- * bit for bit. Frames with w or h == 0 are skipped. The launch sequence for a given frame
- * count, order and flags is captured once into a CUDA graph and replayed; tile shapes come
- * from a built-in autotuner (first call per shape class, unless DFR_AUTOTUNE=0). The frame
- * table is uploaded from library-owned pinned memory into library-owned device memory. */
+/* Reproject n exposures onto one target grid in one CUDA-graph launch (the paper's pipeline
+ * stacks >1000 exposures, Sec. 2). Every frame's pixels are computed with exactly the
+ * arithmetic of dfr_reproject for the same bounding box and flags, so results are equal bit
+ * for bit. Frames with w or h == 0 are skipped. The graph is either the single-frame kernels
+ * in parallel chains or one persistent kernel over a frame table (library-owned pinned and
+ * device memory); a built-in autotuner picks the form on the first call per (order, flags,
+ * SIP degree, log2 n) by timing the candidates on the caller's data (DFR_AUTOTUNE=0: one
+ * chain, no timing). Graphs are cached and updated in place when only pointers change. */
 int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                         int32_t order, uint32_t flags, void* stream);
 
@@ -151,6 +152,27 @@ int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
  * dfr_reproject_batch. */
 int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                                 int32_t order, uint32_t flags, void* stream);
+
+/* Co-add (stack) n exposures onto one target grid: for every target pixel p covered by a
+ * frame, sum_vf[p] += value_f(p) * footprint_f(p) and sum_f[p] += footprint_f(p), with value
+ * and footprint exactly as dfr_reproject computes them (Sec. 3.1); combining reprojected
+ * exposures is the use the paper builds the method for (Sec. 1). Frames are added in order,
+ * one after another (one CUDA-graph launch), each as a single FP32 fused multiply-add per
+ * pixel: the result is deterministic. sum_vf / sum_f: device, tgt->naxis[1] rows of
+ * tgt->naxis[0] values, row stride `pitch` (>= NAXIS1); the caller zeroes them first (or keeps
+ * accumulating across calls). A frame's out / footprint / out_pitch fields are ignored; its
+ * bounding box must lie inside the target grid, and w = h = 0 asks the library to size it
+ * (dfr_target_bbox). Pixels a frame does not cover are not touched. flags as dfr_reproject
+ * (DFR_NO_TMA allowed). Frames share library-owned graph state with dfr_reproject_batch. */
+int dfr_coadd(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt, int32_t order,
+              uint32_t flags, float* sum_vf, float* sum_f, int64_t pitch, void* stream);
+
+/* Mean of a co-add: mean[p] = sum_vf[p] / sum_f[p] where sum_f[p] > min_weight, else 0 (the
+ * value of uncovered pixels in dfr_reproject). Device buffers, h rows of w values, row strides
+ * pitch (sums) and mean_pitch; mean may alias sum_vf when the strides agree. Asynchronous. */
+int dfr_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch, int32_t w,
+                        int32_t h, float min_weight, float* mean, int64_t mean_pitch,
+                        void* stream);
 
 /* Adjoint of dfr_reproject with respect to the source pixels and the source WCS.
  * Given grad_out = dL/d(out) (device, out_h rows, stride go_pitch) for the same arguments as a

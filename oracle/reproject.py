@@ -1,4 +1,5 @@
-"""Oracle reprojection (TEST INFRASTRUCTURE): Sec. 3.1 steps 1-3 per target pixel, FP64.
+"""Oracle reprojection (TEST INFRASTRUCTURE): Sec. 3.1 steps 1-3 per target pixel, FP64, and the
+co-add of several reprojected exposures (the combination the method serves, Sec. 1).
 
 For each target pixel: pixel -> world with the target WCS (Sec. 3.2.1), world -> source pixel
 with the source WCS (Sec. 3.2.2), then interpolation of the source and of the footprint
@@ -83,3 +84,28 @@ def target_bbox(src, tgt, samples=64, margin=2):
     if x1 < x0 or y1 < y0:
         return (0, 0, 0, 0)
     return (x0, y0, x1 - x0 + 1, y1 - y0 + 1)
+
+
+def coadd(frames, tgt, order, pixels=None, inverse="poly"):
+    """Co-add of exposures on the target grid, FP64: for every target pixel the sums over the
+    frames of value * footprint and of footprint, value and footprint as in ``reproject``
+    (a frame contributes 0 where it does not cover the pixel). The mean image is
+    sum_vf / sum_f where sum_f > 0.
+
+    frames: list of (src_wcs, img). pixels: optional (xt, yt) arrays of target pixels; default
+    the whole target grid (NAXIS2 x NAXIS1 arrays). Returns (sum_vf, sum_f)."""
+    if pixels is None:
+        TW, TH = tgt["naxis"]
+        Y, X = np.mgrid[0:TH, 0:TW].astype(np.float64)
+        shape = (TH, TW)
+    else:
+        X = np.asarray(pixels[0], np.float64)
+        Y = np.asarray(pixels[1], np.float64)
+        shape = X.shape
+    sum_vf = np.zeros(X.size)
+    sum_f = np.zeros(X.size)
+    for src, img in frames:
+        val, fp, _, _ = reproject_pixels(src, tgt, img, X.ravel(), Y.ravel(), order, inverse)
+        sum_vf += val * fp
+        sum_f += fp
+    return sum_vf.reshape(shape), sum_f.reshape(shape)

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
-    "calculate_reprojection",
+    "coadd", "coadd_normalize", "calculate_reprojection",
     "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA",
 ]
@@ -91,6 +91,12 @@ def lib():
         L.dfr_reproject_batch_noalloc.argtypes = [ctypes.POINTER(DfrFrame), ctypes.c_int32,
                                                   ctypes.POINTER(DfrWcs), ctypes.c_int32,
                                                   ctypes.c_uint32, ctypes.c_void_p]
+        L.dfr_coadd.argtypes = [ctypes.POINTER(DfrFrame), ctypes.c_int32, ctypes.POINTER(DfrWcs),
+                                ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.dfr_coadd_normalize.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
         L.dfr_device_status.argtypes = [ctypes.c_void_p]
         _LIB = L
@@ -299,6 +305,64 @@ def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=Non
                                              _order(order), _flags(precision, False, True),
                                              _stream_ptr(stream)))
     return outs, fps
+
+
+def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precision="split",
+          sum_vf=None, sum_f=None, stream=None, tma=True):
+    """Co-add exposures onto the target grid (dfr_coadd): sum_vf += value * footprint and
+    sum_f += footprint per target pixel, frames in order. ``sum_vf`` / ``sum_f`` (device,
+    target-sized) are created zeroed when not given. ``bboxes`` default to (0, 0, 0, 0), which
+    lets the library size each frame's box. Returns (sum_vf, sum_f)."""
+    torch = _torch()
+    t = to_c(tgt_wcs)
+    nx, ny = int(t.naxis[0]), int(t.naxis[1])
+    n = len(images)
+    dev = _dev_f32(images[0], "images[0]").device if n else torch.device("cuda")
+    if sum_vf is None:
+        sum_vf = torch.zeros((ny, nx), dtype=torch.float32, device=dev)
+    if sum_f is None:
+        sum_f = torch.zeros_like(sum_vf)
+    sum_vf = _dev_f32(sum_vf, "sum_vf")
+    sum_f = _dev_f32(sum_f, "sum_f")
+    if sum_f.stride(0) != sum_vf.stride(0) or tuple(sum_f.shape) != tuple(sum_vf.shape):
+        raise ValueError("sum_vf and sum_f must share shape and row stride")
+    if tuple(sum_vf.shape) != (ny, nx):
+        raise ValueError("co-add sums must have the target shape (NAXIS2, NAXIS1)")
+    frames = (DfrFrame * max(n, 1))()
+    keep = []
+    for i in range(n):
+        img = _dev_f32(images[i], "images[%d]" % i)
+        keep.append(img)
+        fr = frames[i]
+        fr.wcs = to_c(src_wcs_list[i])
+        fr.img = img.data_ptr()
+        fr.pitch = img.stride(0)
+        fr.out = 0
+        fr.footprint = 0
+        fr.out_pitch = 0
+        bb = bboxes[i] if bboxes is not None else (0, 0, 0, 0)
+        fr.x0, fr.y0, fr.w, fr.h = (int(v) for v in bb)
+    _check(lib().dfr_coadd(frames, n, ctypes.byref(t), _order(order),
+                           _flags(precision, False, tma), ctypes.c_void_p(sum_vf.data_ptr()),
+                           ctypes.c_void_p(sum_f.data_ptr()), sum_vf.stride(0),
+                           _stream_ptr(stream)))
+    return sum_vf, sum_f
+
+
+def coadd_normalize(sum_vf, sum_f, min_weight=0.0, out=None, stream=None):
+    """Mean of a co-add (dfr_coadd_normalize): sum_vf / sum_f where sum_f > min_weight, else 0."""
+    torch = _torch()
+    sum_vf = _dev_f32(sum_vf, "sum_vf")
+    sum_f = _dev_f32(sum_f, "sum_f")
+    if out is None:
+        out = torch.empty_like(sum_vf)
+    out = _dev_f32(out, "out")
+    h, w = sum_vf.shape
+    _check(lib().dfr_coadd_normalize(ctypes.c_void_p(sum_vf.data_ptr()),
+                                     ctypes.c_void_p(sum_f.data_ptr()), sum_vf.stride(0), w, h,
+                                     float(min_weight), ctypes.c_void_p(out.data_ptr()),
+                                     out.stride(0), _stream_ptr(stream)))
+    return out
 
 
 def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinear",

@@ -271,4 +271,6 @@ const void* backward_tile_kernel(int order, int ideg, int fd) {
   }
 }
 
+DFR_DEFINE_STATUS_READER(read_and_clear_status_bwd_tile)
+
 }  // namespace dfr

@@ -15,6 +15,20 @@ namespace dfr {
 // Device status word of this translation unit (each kernel file has its own copy).
 static __device__ int32_t g_status = 0;
 
+// Each translation unit that includes this header has its own status word; this defines the
+// host-side reader (copy out on stream s, then clear if set) for the including unit's word.
+#define DFR_DEFINE_STATUS_READER(fn)                                                        \
+  cudaError_t fn(int32_t* out, cudaStream_t s) {                                           \
+    int32_t zero = 0;                                                                      \
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_status, sizeof(int32_t), 0,           \
+                                              cudaMemcpyDeviceToHost, s);                  \
+    if (e != cudaSuccess) return e;                                                        \
+    e = cudaStreamSynchronize(s);                                                          \
+    if (e != cudaSuccess) return e;                                                        \
+    if (*out != 0) e = cudaMemcpyToSymbol(g_status, &zero, sizeof(int32_t));               \
+    return e;                                                                              \
+  }
+
 constexpr double kR0 = 57.295779513082320876798154814105;  // 180 / pi
 constexpr double kSnap = 1e-9;                               // FP64 integer snap radius, px
 

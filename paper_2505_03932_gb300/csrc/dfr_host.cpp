@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cctype>
 #include <cmath>
 #include <cstdarg>
@@ -970,7 +971,12 @@ int dfr_device_status(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   e = read_and_clear_status_bwd(&b, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
-  const int32_t s = a | b;
+  int32_t c = 0, d = 0;
+  e = read_and_clear_status_bwd_tile(&c, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  e = read_and_clear_status_coadd(&d, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  const int32_t s = a | b | c | d;
   if (s & kStatusTimeout) return fail(DFR_ERR_TIMEOUT, "a bounded device wait gave up");
   if (s & kStatusCheck) return fail(DFR_ERR_DEVICE, "a kernel reported a failed check");
   return DFR_OK;
@@ -1264,6 +1270,71 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   DFR_CUDA(cudaGraphLaunch(g->second, s));
   DFR_CUDA(cudaEventRecord(c.done, s));
   c.pending = true;
+  return DFR_OK;
+}
+
+extern "C" int dfr_coadd(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt, int32_t order,
+                         uint32_t flags, float* sum_vf, float* sum_f, int64_t pitch,
+                         void* stream) {
+  if (n < 0) return fail(DFR_ERR_INVALID_ARG, "negative frame count");
+  if (n == 0) return DFR_OK;
+  if (!frames || !tgt) return fail(DFR_ERR_INVALID_ARG, "NULL frame array or target");
+  if (!sum_vf || !sum_f) return fail(DFR_ERR_INVALID_ARG, "co-add sums must be non-NULL");
+  if (n > (1 << 20)) return fail(DFR_ERR_INVALID_ARG, "too many frames");
+  int rc = check_wcs(tgt, "target");
+  if (rc != DFR_OK) return rc;
+  const int NX = tgt->naxis[0], NY = tgt->naxis[1];
+  if (pitch < NX) return fail(DFR_ERR_INVALID_ARG, "co-add pitch < target NAXIS1");
+  // frame boxes first (host only), then plans and the launch under the context lock
+  std::vector<std::array<int32_t, 4>> boxes(static_cast<size_t>(n));
+  for (int f = 0; f < n; ++f) {
+    const dfr_frame& fr = frames[f];
+    std::array<int32_t, 4> b{fr.x0, fr.y0, fr.w, fr.h};
+    if (fr.w == 0 && fr.h == 0) {
+      rc = dfr_target_bbox(&fr.wcs, tgt, b.data());
+      if (rc != DFR_OK) {
+        g_err = "frame " + std::to_string(f) + ": " + g_err;
+        return rc;
+      }
+    } else if (fr.w < 0 || fr.h < 0 || fr.x0 < 0 || fr.y0 < 0 || int64_t(fr.x0) + fr.w > NX ||
+               int64_t(fr.y0) + fr.h > NY) {
+      return fail(DFR_ERR_INVALID_ARG, "frame %d: bounding box outside the target grid", f);
+    }
+    boxes[size_t(f)] = b;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCtx* cp = nullptr;
+  rc = ensure_ctx(cp, size_t(n));
+  if (rc != DFR_OK) return rc;
+  DeviceCtx& c = *cp;
+  for (int f = 0; f < n; ++f) {
+    const dfr_frame& fr = frames[f];
+    const auto& b = boxes[size_t(f)];
+    float* o = sum_vf + int64_t(b[1]) * pitch + b[0];
+    float* fp = sum_f + int64_t(b[1]) * pitch + b[0];
+    rc = cached_plan(&fr.wcs, tgt, fr.img, fr.pitch, o, fp, pitch, b[0], b[1], b[2], b[3], order,
+                     flags, nullptr, -1, c.h_plans[f]);
+    if (rc != DFR_OK) {
+      g_err = "frame " + std::to_string(f) + ": " + g_err;
+      return rc;
+    }
+    c.h_plans[f].flags |= kFlagAccumulate;
+  }
+  // one chain: frame f + 1 starts after frame f has finished with the sums
+  return launch_fan(c, n, 1, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int dfr_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch,
+                                   int32_t w, int32_t h, float min_weight, float* mean,
+                                   int64_t mean_pitch, void* stream) {
+  if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative size");
+  if (w == 0 || h == 0) return DFR_OK;
+  if (!sum_vf || !sum_f || !mean) return fail(DFR_ERR_INVALID_ARG, "NULL buffer");
+  if (pitch < w || mean_pitch < w) return fail(DFR_ERR_INVALID_ARG, "pitch < width");
+  if (!(min_weight >= 0.f)) return fail(DFR_ERR_INVALID_ARG, "min_weight must be >= 0");
+  cudaError_t e = launch_coadd_normalize(sum_vf, sum_f, pitch, w, h, min_weight, mean,
+                                         mean_pitch, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_coadd_normalize launch");
   return DFR_OK;
 }
 

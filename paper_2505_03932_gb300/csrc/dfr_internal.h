@@ -110,6 +110,10 @@ struct BwdExtra {
   int16_t pmap[kMaxParams];
 };
 
+// Internal plan flag (never part of the public flags): the plan's kernel adds value x footprint
+// and footprint into co-add sums instead of storing value and footprint.
+constexpr uint32_t kFlagAccumulate = 1u << 16;
+
 // Device status word: bit 0 = a bounded wait timed out, bit 1 = internal check failed.
 enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
 
@@ -122,12 +126,18 @@ int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
 int forward_threads_default();
 cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_status_bwd_tile(int32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_status_coadd(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
 int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats);
 int backward_threads_for(const FwdPlan& p0, int fd);
 const void* backward_tile_kernel(int order, int ideg, int fd);  // dfr_bwd_tile.cu
+const void* coadd_kernel(const FwdPlan& p0);                      // dfr_coadd.cu
+cudaError_t launch_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch,
+                                   int32_t w, int32_t h, float min_weight, float* mean,
+                                   int64_t mean_pitch, cudaStream_t s);
 
 // Plan-builder access for translation units other than dfr_host.cpp.
 int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint32_t flags,

@@ -149,3 +149,37 @@ def test_argument_errors_before_any_launch(dfr):
     assert call(w=0, h=0, img=None, out=None) == 0
     assert L.dfr_reproject_batch(None, 0, ctypes.byref(t), 1, 1, None) == 0
     assert L.dfr_reproject_batch(None, 3, ctypes.byref(t), 1, 1, None) == -1
+
+
+def test_coadd_argument_errors_before_any_launch(dfr):
+    L = dfr.lib()
+    t = dfr.to_c(synth.tan_wcs(64, 48))
+    dummy = ctypes.c_void_p(16)
+    frames = (dfr.DfrFrame * 2)()
+    for fr in frames:
+        fr.wcs = dfr.to_c(synth.tan_wcs(40, 30))
+        fr.img = 16
+        fr.pitch = 40
+        fr.x0, fr.y0, fr.w, fr.h = 0, 0, 20, 20
+    co = lambda n=2, vf=dummy, f=dummy, pitch=64, fr=frames: L.dfr_coadd(
+        fr, n, ctypes.byref(t), 1, 1, vf, f, pitch, None)
+    assert co(n=0) == 0
+    assert co(n=-1) == -1
+    assert co(vf=None) == -1
+    assert co(f=None) == -1
+    assert co(pitch=63) == -1
+    frames[1].x0 = 50  # 50 + 20 > NAXIS1 = 64
+    assert co() == -1
+    assert "outside the target grid" in L.dfr_last_error().decode()
+    frames[1].x0, frames[1].y0 = 0, -1
+    assert co() == -1
+    nz = lambda **kw: L.dfr_coadd_normalize(
+        kw.get("vf", dummy), kw.get("f", dummy), kw.get("pitch", 64), kw.get("w", 64),
+        kw.get("h", 48), kw.get("mw", 0.0), kw.get("mean", dummy), kw.get("mp", 64), None)
+    assert nz(w=0) == 0
+    assert nz(w=-1) == -1
+    assert nz(mean=None) == -1
+    assert nz(pitch=10) == -1
+    assert nz(mp=10) == -1
+    assert nz(mw=-1.0) == -1
+    assert nz(mw=float("nan")) == -1
