@@ -94,9 +94,14 @@ int dfr_abi_version(void);
  * Sec. 3.1 lists the keywords used). `cards` holds 80-character cards, either packed or
  * newline-separated; `nbytes` is its length. Keywords: NAXISn, CTYPEn (RA---TAN / DEC--TAN,
  * optional -SIP), CRPIXn, CRVALn, CDi_j or PCi_j with CDELTi (CD wins; CD = CDELT x PC,
- * Sec. 3.1), optional LONPOLE (must be 180), A_ORDER/A_p_q, B_*, AP_*, BP_*. Missing
- * keywords -> DFR_ERR_HEADER_PARSE; other projections -> DFR_ERR_UNSUPPORTED_WCS; singular
- * CD -> DFR_ERR_SINGULAR_CD. `out` is fully written on success, untouched on failure. */
+ * Sec. 3.1) or, with neither CD nor PC, CDELTi with the legacy CROTA2 rotation
+ * (CD = [[CDELT1 cos r, -CDELT2 sin r], [CDELT1 sin r, CDELT2 cos r]]), optional LONPOLE,
+ * A_ORDER/A_p_q, B_*, AP_*, BP_*. The record has no LONPOLE field: the method's formulas fix
+ * the native pole longitude at 180 deg (Sec. 3.2), and another LONPOLE (a rotation of the
+ * native longitude, which for the zenithal TAN is a rotation of the intermediate plane after
+ * CD) is folded into CD. Missing keywords -> DFR_ERR_HEADER_PARSE; other projections ->
+ * DFR_ERR_UNSUPPORTED_WCS; singular CD -> DFR_ERR_SINGULAR_CD. `out` is fully written on
+ * success, untouched on failure. */
 int dfr_wcs_from_header(const char* cards, size_t nbytes, dfr_wcs* out);
 
 /* Fit inverse SIP polynomials AP/BP of the given order (1..9) to the forward A/B of `wcs`

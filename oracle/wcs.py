@@ -32,6 +32,10 @@ Readings taken where the paper is ambiguous (each is listed in the design notes)
     (cos th sin phi, cos th cos phi for theta; the ra arguments for dec), so the oracle computes
     the same angle as atan2(z, hypot(x, y)). ``theta_mode="asin"`` keeps the printed form.
   * A target point is covered by the source only where the source sin(theta) > 0.
+  * LONPOLE (the native longitude of the celestial pole, phi_p) is 180 deg in the paper's
+    formulas. A record may carry another value as ``lonpole``: the rotation steps then use
+    phi - (phi_p - 180 deg) in place of phi (the paper's phi is the standard native longitude
+    minus 180 deg), as in the general zenithal case of FITS WCS Paper II.
 
 All functions are written over a math namespace ``m`` (numpy by default) so that the same code
 runs on forward-mode dual numbers (oracle.dual) for gradients.
@@ -97,6 +101,11 @@ def cd_inverse(cd):
     return [[d / det, -b / det], [-c / det, a / det]]
 
 
+def _lonpole_offset(w):
+    """phi_p - 180 deg in radians (0 for the paper's phi_p = 180 deg)."""
+    return (float(w.get("lonpole", 180.0)) - 180.0) * DEG
+
+
 # ------------------------------------------------------------------------------ Sec. 3.2.1
 def pix2world(w, x, y, m=np, theta_mode="atan2"):
     """Target pixel (0-based x, y) -> (ra, dec) in degrees, Sec. 3.2.1."""
@@ -117,7 +126,7 @@ def pix2world(w, x, y, m=np, theta_mode="atan2"):
     vp = cd[1][0] * u + cd[1][1] * v
     # gnomonic deprojection to native spherical coordinates
     r = m.sqrt(up * up + vp * vp)
-    phi = m.arctan2(-up, vp)
+    phi = m.arctan2(-up, vp) - _lonpole_offset(w)
     theta = m.arctan2(R0 + 0.0 * r, r)
     # native -> celestial
     st, ct = m.sin(theta), m.cos(theta)
@@ -150,7 +159,7 @@ def world_to_intermediate(w, ra_deg, dec_deg, m=np, theta_mode="atan2"):
     n1 = -cdn * sdra
     n2 = sd * cd0 - cdn * sd0 * cdra
     dd = sd * sd0 + cdn * cd0 * cdra
-    phi = m.arctan2(n1, n2)
+    phi = m.arctan2(n1, n2) + _lonpole_offset(w)
     if theta_mode == "asin":
         theta = m.arcsin(dd)
     else:
@@ -322,8 +331,9 @@ def _parse_value(s):
 
 
 def parse_header(text):
-    """FITS header cards -> WCS record. CD wins over PC x CDELT; LONPOLE must be 180 if given;
-    CTYPE must be RA---TAN / DEC--TAN with an optional -SIP suffix."""
+    """FITS header cards -> WCS record. CD wins over PC x CDELT, which wins over CDELT with the
+    legacy CROTA2 rotation; LONPOLE other than 180 is kept in the record (``lonpole``); CTYPE
+    must be RA---TAN / DEC--TAN with an optional -SIP suffix."""
     cards = {}
     for rec in _records(text):
         key = rec[:8].strip()
@@ -339,16 +349,27 @@ def parse_header(text):
     if c1[:8] != "RA---TAN" or c2[:8] != "DEC--TAN" or c1[8:] not in ("", "-SIP") \
             or c2[8:] not in ("", "-SIP"):
         raise HeaderError("unsupported CTYPE")
-    if "LONPOLE" in cards and float(cards["LONPOLE"]) != 180.0:
-        raise HeaderError("unsupported LONPOLE")
+    for k in ("LONPOLE", "CROTA2"):
+        if k in cards and (isinstance(cards[k], (str, bool))):
+            raise HeaderError("%s is not a number" % k)
+    lonpole = float(cards.get("LONPOLE", 180.0))
+    if not math.isfinite(lonpole):
+        raise HeaderError("bad LONPOLE")
+    has_pc = any(k in cards for k in ("PC1_1", "PC1_2", "PC2_1", "PC2_2"))
     if any(k in cards for k in ("CD1_1", "CD1_2", "CD2_1", "CD2_2")):
         cd = [[float(cards.get("CD1_1", 0.0)), float(cards.get("CD1_2", 0.0))],
               [float(cards.get("CD2_1", 0.0)), float(cards.get("CD2_2", 0.0))]]
     elif "CDELT1" in cards and "CDELT2" in cards:
-        pc = [[float(cards.get("PC1_1", 1.0)), float(cards.get("PC1_2", 0.0))],
-              [float(cards.get("PC2_1", 0.0)), float(cards.get("PC2_2", 1.0))]]
         d = [float(cards["CDELT1"]), float(cards["CDELT2"])]
-        cd = [[d[0] * pc[0][0], d[0] * pc[0][1]], [d[1] * pc[1][0], d[1] * pc[1][1]]]
+        if not has_pc and "CROTA2" in cards:
+            # legacy AIPS rotation (FITS WCS Paper II, Sec. 6.1): CD = diag(CDELT) rotated
+            rho = float(cards["CROTA2"]) * DEG
+            cd = [[d[0] * math.cos(rho), -d[1] * math.sin(rho)],
+                  [d[0] * math.sin(rho), d[1] * math.cos(rho)]]
+        else:
+            pc = [[float(cards.get("PC1_1", 1.0)), float(cards.get("PC1_2", 0.0))],
+                  [float(cards.get("PC2_1", 0.0)), float(cards.get("PC2_2", 1.0))]]
+            cd = [[d[0] * pc[0][0], d[0] * pc[0][1]], [d[1] * pc[1][0], d[1] * pc[1][1]]]
     else:
         raise HeaderError("no CD or CDELT")
     if cd[0][0] * cd[1][1] - cd[0][1] * cd[1][0] == 0.0:
@@ -359,6 +380,8 @@ def parse_header(text):
         "crval": (float(cards["CRVAL1"]), float(cards["CRVAL2"])),
         "cd": cd,
     }
+    if lonpole != 180.0:
+        w["lonpole"] = lonpole
     for name in ("A", "B", "AP", "BP"):
         order = int(cards.get(name + "_ORDER", 0))
         if order < 0 or order > MAX_SIP:

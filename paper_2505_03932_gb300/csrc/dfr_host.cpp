@@ -721,9 +721,13 @@ int dfr_wcs_from_header(const char* cards, size_t nbytes, dfr_wcs* out) {
   if (!tan_ok(c1, "RA---TAN") || !tan_ok(c2, "DEC--TAN"))
     return fail(DFR_ERR_UNSUPPORTED_WCS, "CTYPE %s/%s: only RA---TAN/DEC--TAN[-SIP]", c1.c_str(),
                 c2.c_str());
-  double lonpole;
-  if (num("LONPOLE", lonpole) && lonpole != 180.0)
-    return fail(DFR_ERR_UNSUPPORTED_WCS, "LONPOLE %g: only 180 is supported", lonpole);
+  for (const char* k : {"LONPOLE", "CROTA2"}) {
+    auto it = kv.find(k);
+    if (it != kv.end() && it->second.is_str) return fail(DFR_ERR_HEADER_PARSE, "%s is not a number", k);
+  }
+  double lonpole = 180.0;
+  num("LONPOLE", lonpole);
+  if (!std::isfinite(lonpole)) return fail(DFR_ERR_HEADER_PARSE, "non-finite LONPOLE");
   w.naxis[0] = int32_t(n1);
   w.naxis[1] = int32_t(n2);
   const bool has_cd = kv.count("CD1_1") || kv.count("CD1_2") || kv.count("CD2_1") ||
@@ -740,13 +744,39 @@ int dfr_wcs_from_header(const char* cards, size_t nbytes, dfr_wcs* out) {
     double d1, d2;
     if (!num("CDELT1", d1) || !num("CDELT2", d2))
       return fail(DFR_ERR_HEADER_PARSE, "no CDi_j and no CDELT1/CDELT2");
-    double pc[2][2] = {{1.0, 0.0}, {0.0, 1.0}};
-    const char* ks[2][2] = {{"PC1_1", "PC1_2"}, {"PC2_1", "PC2_2"}};
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) num(ks[i][j], pc[i][j]);
-    const double d[2] = {d1, d2};
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) w.cd[i][j] = d[i] * pc[i][j];
+    const bool has_pc = kv.count("PC1_1") || kv.count("PC1_2") || kv.count("PC2_1") ||
+                        kv.count("PC2_2");
+    double crota2 = 0.0;
+    if (!has_pc && num("CROTA2", crota2)) {
+      // legacy rotation keyword: CD = [[CDELT1 cos r, -CDELT2 sin r], [CDELT1 sin r, CDELT2 cos r]]
+      const double r = crota2 * (kPi / 180.0);
+      w.cd[0][0] = d1 * std::cos(r);
+      w.cd[0][1] = -d2 * std::sin(r);
+      w.cd[1][0] = d1 * std::sin(r);
+      w.cd[1][1] = d2 * std::cos(r);
+    } else {
+      double pc[2][2] = {{1.0, 0.0}, {0.0, 1.0}};
+      const char* ks[2][2] = {{"PC1_1", "PC1_2"}, {"PC2_1", "PC2_2"}};
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) num(ks[i][j], pc[i][j]);
+      const double d[2] = {d1, d2};
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) w.cd[i][j] = d[i] * pc[i][j];
+    }
+  }
+  if (lonpole != 180.0) {
+    // TAN is zenithal: a native pole longitude phi_p other than 180 deg rotates the native
+    // longitude by phi_p - 180 deg, which is the rotation of the intermediate plane
+    // (u', v') -> (c u' + s v', -s u' + c v') after CD (SIP acts before CD). The record keeps
+    // phi_p = 180 deg with that rotation folded into CD.
+    const double t = (lonpole - 180.0) * (kPi / 180.0);
+    const double c = std::cos(t), sn = std::sin(t);
+    double r[2][2];
+    for (int j = 0; j < 2; ++j) {
+      r[0][j] = c * w.cd[0][j] + sn * w.cd[1][j];
+      r[1][j] = -sn * w.cd[0][j] + c * w.cd[1][j];
+    }
+    std::memcpy(w.cd, r, sizeof(r));
   }
   const double det = w.cd[0][0] * w.cd[1][1] - w.cd[0][1] * w.cd[1][0];
   if (!(det != 0.0) || !std::isfinite(det)) return fail(DFR_ERR_SINGULAR_CD, "CD is singular");

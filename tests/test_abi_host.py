@@ -70,7 +70,7 @@ def test_header_pc_cdelt(dfr):
 
 @pytest.mark.parametrize("edit,code", [
     (lambda t: t.replace("RA---TAN", "RA---SIN"), -3),
-    (lambda t: t.replace("END", "LONPOLE =                170.0\nEND"), -3),
+    (lambda t: t.replace("END", "LONPOLE = 'abc'\nEND"), -2),
     (lambda t: "\n".join(l for l in t.split("\n") if not l.startswith("CRPIX1")), -2),
     (lambda t: "\n".join(l for l in t.split("\n") if not l.startswith("CD")), -2),
     (lambda t: re.sub(r"CD2_2   =\s*\S+", "CD2_2   = 0.0", re.sub(r"CD1_1   =\s*\S+",
@@ -183,3 +183,49 @@ def test_coadd_argument_errors_before_any_launch(dfr):
     assert nz(mp=10) == -1
     assert nz(mw=-1.0) == -1
     assert nz(mw=float("nan")) == -1
+
+
+def _cards_without_cd(w):
+    return [ln for ln in synth.header_cards(w, "\n").split("\n") if not ln.startswith("CD")]
+
+
+def test_header_crota2_matches_the_cdelt_rotation_convention(dfr):
+    """CDELT + CROTA2 (no CD, no PC) -> CD of the CROTA2 convention, which is how the synthetic
+    WCS records build their CD from (scale, rotation)."""
+    s = 2.5 / 3600
+    for rho in (0.0, 1.2, -37.5, 90.0):
+        w = synth.tan_wcs(100, 80, rho_deg=rho)
+        text = "\n".join(_cards_without_cd(w)[:-1] + ["CDELT1  = %.17g" % -s,
+                                                      "CDELT2  = %.17g" % s,
+                                                      "CROTA2  = %.17g" % rho, "END"])
+        for got in (dfr.wcs_from_header(text)["cd"], OW.parse_header(text)["cd"]):
+            assert np.allclose(got, w["cd"], rtol=0, atol=1e-18)
+    # PC wins over CROTA2
+    text = "\n".join(_cards_without_cd(synth.tan_wcs(100, 80))[:-1] + [
+        "CDELT1  = -0.001", "CDELT2  = 0.002", "CROTA2  = 30.0", "PC1_1   = 1.0", "END"])
+    assert dfr.wcs_from_header(text)["cd"] == [[-0.001, 0.0], [0.0, 0.002]]
+
+
+def test_header_lonpole_folded_into_cd_maps_like_the_oracle(dfr):
+    """LONPOLE != 180: the library folds the native-longitude rotation into CD; the oracle keeps
+    LONPOLE and rotates on the sphere. Both records give the same sky positions (1e-12 deg) and
+    the same source pixels."""
+    rng = synth.rng_for(17)
+    base = synth.add_sip(synth.tan_wcs(300, 200, crval=(210.0, 47.0), rho_deg=3.0), 3, 1e-6, rng)
+    text0 = synth.header_cards(base, "\n")
+    X = rng.uniform(-50, 350, 400)
+    Y = rng.uniform(-50, 250, 400)
+    for lon in (170.0, 0.0, 245.5, -90.0):
+        text = text0.replace("END", "LONPOLE = %.17g\nEND" % lon)
+        c = dfr.wcs_from_header(text)
+        o = OW.parse_header(text)
+        assert o["lonpole"] == lon and "lonpole" not in c
+        ra_c, dec_c = OW.pix2world(c, X, Y)
+        ra_o, dec_o = OW.pix2world(o, X, Y)
+        dra = (ra_c - ra_o + 180.0) % 360.0 - 180.0
+        assert np.abs(dra * np.cos(np.radians(dec_o))).max() < 1e-12
+        assert np.abs(dec_c - dec_o).max() < 1e-12
+        u_c, v_c, ok_c = OW.world_to_intermediate(c, ra_o, dec_o)
+        u_o, v_o, ok_o = OW.world_to_intermediate(o, ra_o, dec_o)
+        assert np.array_equal(ok_c, ok_o)
+        assert np.abs(u_c - u_o).max() < 1e-9 and np.abs(v_c - v_o).max() < 1e-9

@@ -208,3 +208,30 @@ def test_config1_full_size_sampled():
     # the bench call (no coordinate output) writes the same values
     v2, f2 = dfr().reproject(img_d, src, tgt, bbox=bbox, order="bicubic", precision="split")
     assert np.array_equal(v2.cpu().numpy(), val) and np.array_equal(f2.cpu().numpy(), fp)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_legacy_header_keywords_lonpole_crota2(precision):
+    """Headers with CDELT + CROTA2 (no CD) and LONPOLE != 180 on both sides: parsed by the
+    library (LONPOLE folded into CD), reprojected on the GPU, against the oracle on its own
+    parse of the same text (LONPOLE kept, rotation on the sphere)."""
+    src, tgt, img = _small_sip(w=400, h=300, seed=12)
+    s = 2.5 / 3600
+
+    def legacy(w, rho, scale, lonpole):
+        lines = [ln for ln in synth.header_cards(w, "\n").split("\n") if not ln.startswith("CD")]
+        return "\n".join(lines[:-1] + ["CDELT1  = %.17g" % (-s * scale),
+                                       "CDELT2  = %.17g" % (s * scale),
+                                       "CROTA2  = %.17g" % rho, "LONPOLE = %.17g" % lonpole,
+                                       "END"])
+
+    ts, tt = legacy(src, 0.0, 1.0, 215.0), legacy(tgt, 1.2, 1.01, 150.0)
+    c_src, c_tgt = dfr().wcs_from_header(ts), dfr().wcs_from_header(tt)
+    o_src, o_tgt = OW.parse_header(ts), OW.parse_header(tt)
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    val, fp, cr = gpu(c_src, c_tgt, to_dev(img), "bicubic", precision, bbox)
+    dmax, _ = coord_check(o_src, o_tgt, cr, bbox)
+    assert dmax < (FP64_PX if precision == "fp64" else SPLIT_PX)
+    e, fe = value_check(img, "bicubic", val, fp, cr, precision)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    assert (fp > 0).mean() > 0.5

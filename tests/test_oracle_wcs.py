@@ -283,7 +283,34 @@ def test_header_pc_cdelt_and_errors():
     assert w["cd"] == [[-0.0005, -0.00025], [-0.0005, 0.001]]
     with pytest.raises(W.HeaderError):
         W.parse_header(base.replace("RA---TAN", "RA---SIN"))
-    with pytest.raises(W.HeaderError):
-        W.parse_header(base.replace("END", "LONPOLE =                 170.\nEND"))
+    assert W.parse_header(base.replace("END", "LONPOLE =                 170.\nEND"))[
+        "lonpole"] == 170.0
     with pytest.raises(W.HeaderError):
         W.parse_header("\n".join(lines))
+
+
+def test_lonpole_is_a_rotation_of_the_intermediate_plane():
+    """General phi_p (LONPOLE) on the sphere equals phi_p = 180 deg with the intermediate plane
+    rotated: the paper's native longitude is phi = atan2(-u', v'), so phi - d is the longitude of
+    (u' cos d + v' sin d, -u' sin d + v' cos d). Both directions, 1e-12 deg / 1e-9 px, and the
+    pixel -> world -> pixel round trip of the LONPOLE record."""
+    rng = np.random.default_rng(5)
+    w = _wcs()
+    X = rng.uniform(-100, 600, 500)
+    Y = rng.uniform(-100, 500, 500)
+    for lon in (0.0, 100.0, 181.5, 300.0):
+        d = np.radians(lon - 180.0)
+        wl = dict(w, lonpole=lon)
+        cd = np.array(w["cd"])
+        rot = np.array([[np.cos(d), np.sin(d)], [-np.sin(d), np.cos(d)]]) @ cd
+        wr = dict(w, cd=rot.tolist())
+        ra_l, dec_l = W.pix2world(wl, X, Y)
+        ra_r, dec_r = W.pix2world(wr, X, Y)
+        dra = (ra_l - ra_r + 180.0) % 360.0 - 180.0
+        assert np.abs(dra * np.cos(np.radians(dec_r))).max() < 1e-12
+        assert np.abs(dec_l - dec_r).max() < 1e-12
+        x, y, ok = W.world2pix(wl, ra_l, dec_l)
+        assert ok.all() and np.abs(x - X).max() < 1e-9 and np.abs(y - Y).max() < 1e-9
+        u_l, v_l, _ = W.world_to_intermediate(wl, ra_r, dec_r)
+        u_r, v_r, _ = W.world_to_intermediate(wr, ra_r, dec_r)
+        assert np.abs(u_l - u_r).max() < 1e-9 and np.abs(v_l - v_r).max() < 1e-9
