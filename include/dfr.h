@@ -60,6 +60,8 @@ extern "C" {
 #define DFR_SPLIT          1u  /* FP64 sky rotation at per-tile anchors, FP32 per pixel      */
 #define DFR_EXACT_INVERSE  2u  /* source inverse = Newton solve of A/B (AP/BP as start)      */
 #define DFR_NO_TMA         4u  /* gather straight from global memory instead of TMA tiles    */
+#define DFR_NAN_MASK       8u  /* NaN source pixels are missing: no weight in value or        */
+                               /* footprint (forward and co-add; not the adjoint)             */
 
 #define DFR_MAX_SIP 9
 
@@ -121,7 +123,8 @@ int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]);
  * Sec. 3.2). src_img: device, src->naxis[1] rows, row stride src_pitch. out: device,
  * out_h rows of out_w values, row stride out_pitch. footprint: device, same layout, nullable.
  * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC. flags: DFR_FP64 or DFR_SPLIT, optionally
- * | DFR_EXACT_INVERSE | DFR_NO_TMA. coords_out (nullable, device): 2*out_w*out_h doubles,
+ * | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK. Without DFR_NAN_MASK, NaN source pixels
+ * propagate into the values they touch. coords_out (nullable, device): 2*out_w*out_h doubles,
  * the source position (x then y per pixel, row-major) exactly as the kernel used it, NaN where
  * the projection is undefined. Asynchronous on `stream`; out/footprint are written in full. */
 int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,

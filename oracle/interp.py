@@ -67,8 +67,12 @@ def covered(img_shape, x, y, valid=None):
     return ok
 
 
-def interpolate(img, x, y, order, valid=None, a=-0.5, use_snap=True):
-    """Value and footprint of ``img`` (H x W) at positions (x, y). Returns float64 arrays."""
+def interpolate(img, x, y, order, valid=None, a=-0.5, use_snap=True, nan_mask=False):
+    """Value and footprint of ``img`` (H x W) at positions (x, y). Returns float64 arrays.
+
+    nan_mask: NaN source pixels count as missing, like pixels outside the image: they take no
+    weight in the value or the footprint. A pixel is then covered only where the remaining
+    weight is positive (bicubic weights can be negative, so masking may leave a sum <= 0)."""
     img = np.asarray(img)
     H, W = img.shape
     x = np.asarray(x, dtype=np.float64)
@@ -90,9 +94,11 @@ def interpolate(img, x, y, order, valid=None, a=-0.5, use_snap=True):
             inside = iny & (xx >= 0) & (xx < W) & ok
             w = wx[i] * wy[j]
             s = img[np.clip(yy, 0, H - 1), np.clip(xx, 0, W - 1)].astype(np.float64)
+            if nan_mask:
+                inside = inside & ~np.isnan(s)
             num += np.where(inside, w * s, 0.0)
             fp += np.where(inside, w, 0.0)
-    live = ok & (fp != 0.0)
+    live = ok & ((fp > 0.0) if nan_mask else (fp != 0.0))
     val = np.where(live, num / np.where(live, fp, 1.0), 0.0)
     fp = np.where(live, fp, 0.0)
     return val, fp

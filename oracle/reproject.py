@@ -28,8 +28,10 @@ def coords(src, tgt, xt, yt, inverse="poly"):
                               inverse=inverse)
 
 
-def reproject_pixels(src, tgt, img, xt, yt, order, inverse="poly", use_snap=True):
-    """Value, footprint, x_s, y_s at an explicit list of target pixels."""
+def reproject_pixels(src, tgt, img, xt, yt, order, inverse="poly", use_snap=True,
+                     nan_mask=False):
+    """Value, footprint, x_s, y_s at an explicit list of target pixels (nan_mask: NaN source
+    pixels are missing, see interp.interpolate)."""
     order = _order(order)
     xt = np.asarray(xt, np.float64).ravel()
     yt = np.asarray(yt, np.float64).ravel()
@@ -42,12 +44,13 @@ def reproject_pixels(src, tgt, img, xt, yt, order, inverse="poly", use_snap=True
         x, y, ok = coords(src, tgt, xt[s:e], yt[s:e], inverse)
         x = np.where(ok, x, np.nan)
         y = np.where(ok, y, np.nan)
-        val[s:e], fp[s:e] = _interp.interpolate(img, x, y, order, valid=ok, use_snap=use_snap)
+        val[s:e], fp[s:e] = _interp.interpolate(img, x, y, order, valid=ok, use_snap=use_snap,
+                                                nan_mask=nan_mask)
         xs[s:e], ys[s:e] = x, y
     return val, fp, xs, ys
 
 
-def reproject(src, tgt, img, order, bbox=None, inverse="poly", use_snap=True):
+def reproject(src, tgt, img, order, bbox=None, inverse="poly", use_snap=True, nan_mask=False):
     """Reproject ``img`` (source WCS ``src``) onto the target grid ``tgt``.
 
     bbox = (x0, y0, w, h) in target pixels; default the whole target (NAXIS1 x NAXIS2).
@@ -57,7 +60,7 @@ def reproject(src, tgt, img, order, bbox=None, inverse="poly", use_snap=True):
     x0, y0, w, h = bbox
     X, Y = np.meshgrid(np.arange(x0, x0 + w, dtype=np.float64),
                        np.arange(y0, y0 + h, dtype=np.float64))
-    val, fp, xs, ys = reproject_pixels(src, tgt, img, X, Y, order, inverse, use_snap)
+    val, fp, xs, ys = reproject_pixels(src, tgt, img, X, Y, order, inverse, use_snap, nan_mask)
     return (val.reshape(h, w), fp.reshape(h, w), xs.reshape(h, w), ys.reshape(h, w))
 
 
@@ -86,7 +89,7 @@ def target_bbox(src, tgt, samples=64, margin=2):
     return (x0, y0, x1 - x0 + 1, y1 - y0 + 1)
 
 
-def coadd(frames, tgt, order, pixels=None, inverse="poly"):
+def coadd(frames, tgt, order, pixels=None, inverse="poly", nan_mask=False):
     """Co-add of exposures on the target grid, FP64: for every target pixel the sums over the
     frames of value * footprint and of footprint, value and footprint as in ``reproject``
     (a frame contributes 0 where it does not cover the pixel). The mean image is
@@ -105,7 +108,8 @@ def coadd(frames, tgt, order, pixels=None, inverse="poly"):
     sum_vf = np.zeros(X.size)
     sum_f = np.zeros(X.size)
     for src, img in frames:
-        val, fp, _, _ = reproject_pixels(src, tgt, img, X.ravel(), Y.ravel(), order, inverse)
+        val, fp, _, _ = reproject_pixels(src, tgt, img, X.ravel(), Y.ravel(), order, inverse,
+                                         nan_mask=nan_mask)
         sum_vf += val * fp
         sum_f += fp
     return sum_vf.reshape(shape), sum_f.reshape(shape)

@@ -21,11 +21,11 @@ __all__ = [
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
     "coadd", "coadd_normalize", "calculate_reprojection",
     "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "FP64", "SPLIT",
-    "EXACT_INVERSE", "NO_TMA",
+    "EXACT_INVERSE", "NO_TMA", "NAN_MASK",
 ]
 
 NEAREST, BILINEAR, BICUBIC = 0, 1, 2
-FP64, SPLIT, EXACT_INVERSE, NO_TMA = 0, 1, 2, 4
+FP64, SPLIT, EXACT_INVERSE, NO_TMA, NAN_MASK = 0, 1, 2, 4, 8
 ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.environ.get("DFR_LIBRARY") or os.path.join(_HERE, "libdfr.so")
@@ -200,7 +200,7 @@ def _dev_f32(t, name):
     return t
 
 
-def _flags(precision, exact_inverse, tma):
+def _flags(precision, exact_inverse, tma, nan_mask=False):
     f = SPLIT if precision == "split" else FP64
     if precision not in ("split", "fp64"):
         raise ValueError("precision must be 'split' or 'fp64'")
@@ -208,6 +208,8 @@ def _flags(precision, exact_inverse, tma):
         f |= EXACT_INVERSE
     if not tma:
         f |= NO_TMA
+    if nan_mask:
+        f |= NAN_MASK
     return f
 
 
@@ -217,11 +219,12 @@ def _order(order):
 
 def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilinear",
               precision="split", exact_inverse=False, footprint=True, coords=False, tma=True,
-              out=None, fp_out=None, stream=None):
+              out=None, fp_out=None, stream=None, nan_mask=False):
     """Reproject a device image onto the target grid (dfr_reproject).
 
     shape_out (h, w) defaults to the target NAXIS; bbox = (x0, y0, w, h) selects part of the
-    target grid. Returns (value, footprint or None[, coords (h, w, 2) float64])."""
+    target grid; nan_mask: NaN source pixels are missing (no weight). Returns (value, footprint
+    or None[, coords (h, w, 2) float64])."""
     torch = _torch()
     src_img = _dev_f32(src_img, "src_img")
     if bbox is None:
@@ -243,13 +246,14 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
         ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)), ctypes.c_void_p(src_img.data_ptr()),
         src_img.stride(0), ctypes.c_void_p(out.data_ptr()),
         ctypes.c_void_p(fp.data_ptr() if fp is not None else 0), out.stride(0), x0, y0, w, h,
-        _order(order), _flags(precision, exact_inverse, tma),
+        _order(order), _flags(precision, exact_inverse, tma, nan_mask),
         ctypes.c_void_p(cr.data_ptr() if cr is not None else 0), _stream_ptr(stream)))
     return (out, fp, cr) if coords else (out, fp)
 
 
 def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear",
-                    precision="split", outs=None, fps=None, footprint=True, stream=None):
+                    precision="split", outs=None, fps=None, footprint=True, stream=None,
+                    nan_mask=False):
     """Reproject many exposures in one persistent launch (dfr_reproject_batch).
 
     bboxes default to dfr_target_bbox per frame. Returns (values, footprints) lists."""
@@ -277,7 +281,8 @@ def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear"
         vals.append(o)
         fpl.append(f)
     _check(lib().dfr_reproject_batch(frames, n, ctypes.byref(to_c(tgt_wcs)), _order(order),
-                                     _flags(precision, False, True), _stream_ptr(stream)))
+                                     _flags(precision, False, True, nan_mask),
+                                     _stream_ptr(stream)))
     return vals, fpl
 
 
@@ -308,7 +313,7 @@ def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=Non
 
 
 def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precision="split",
-          sum_vf=None, sum_f=None, stream=None, tma=True):
+          sum_vf=None, sum_f=None, stream=None, tma=True, nan_mask=False):
     """Co-add exposures onto the target grid (dfr_coadd): sum_vf += value * footprint and
     sum_f += footprint per target pixel, frames in order. ``sum_vf`` / ``sum_f`` (device,
     target-sized) are created zeroed when not given. ``bboxes`` default to (0, 0, 0, 0), which
@@ -343,7 +348,8 @@ def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precisio
         bb = bboxes[i] if bboxes is not None else (0, 0, 0, 0)
         fr.x0, fr.y0, fr.w, fr.h = (int(v) for v in bb)
     _check(lib().dfr_coadd(frames, n, ctypes.byref(t), _order(order),
-                           _flags(precision, False, tma), ctypes.c_void_p(sum_vf.data_ptr()),
+                           _flags(precision, False, tma, nan_mask),
+                           ctypes.c_void_p(sum_vf.data_ptr()),
                            ctypes.c_void_p(sum_f.data_ptr()), sum_vf.stride(0),
                            _stream_ptr(stream)))
     return sum_vf, sum_f

@@ -72,21 +72,28 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
         sx += wx[a];
         sy += wy[a];
       }
+      const bool mask = (P.flags & DFR_NAN_MASK) != 0;
+      double fm = 0.0;  // masked footprint
 #pragma unroll
       for (int b = 0; b < T::n; ++b) {
-        double row = 0.0;
+        double row = 0.0, rowf = 0.0;
         const int yy = iy + b;
         if (wy[b] != 0.0) {
 #pragma unroll
           for (int a = 0; a < T::n; ++a) {
             const int xx = ix + a;
-            if (wx[a] != 0.0) row += wx[a] * double(__ldg(P.img + int64_t(yy) * P.pitch + xx));
+            if (wx[a] == 0.0) continue;
+            const double s = double(__ldg(P.img + int64_t(yy) * P.pitch + xx));
+            if (mask && s != s) continue;  // NaN tap: missing
+            row += wx[a] * s;
+            rowf += wx[a];
           }
         }
         num += wy[b] * row;
+        fm += wy[b] * rowf;
       }
-      const double f = sx * sy;
-      if (f != 0.0) {
+      const double f = mask ? fm : sx * sy;
+      if (mask ? f > 0.0 : f != 0.0) {
         val = float(num / f);
         fpv = float(f);
       }
@@ -172,16 +179,66 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
   return make_float2((f == 1.f) ? num : __fdividef(num, f), f);
 }
 
+// NaN-masked form (DFR_NAN_MASK): a tap whose source value is NaN is missing, like a tap
+// outside the image. Footprint = sum of the weights of the in-image finite taps, value =
+// sum w S / footprint; both 0 unless that sum is positive (signed bicubic weights can leave a
+// sum <= 0 once taps are missing). Per tap: row_k = sum_q m_kq wx_q S_kq and
+// rowf_k = sum_q m_kq wx_q (m = 0 or 1), then sum_k wy_k row_k and sum_k wy_k rowf_k.
+template <int ORDER, typename Tap>
+__device__ __forceinline__ float2 interp_pixel_masked(float x, float y, int bx, int by, int W,
+                                                      int H, const Tap& S) {
+  using T = Taps<ORDER>;
+  const float flx = floorf(x), fly = floorf(y);
+  const float2 t = make_float2(x - flx, y - fly);
+  int ix = int(flx), iy = int(fly);
+  if (ORDER == DFR_NEAREST) {
+    ix += t.x >= 0.5f;
+    iy += t.y >= 0.5f;
+  }
+  ix += bx + T::lo;
+  iy += by + T::lo;
+  if (ORDER == DFR_NEAREST) {
+    const bool in = unsigned(ix) < unsigned(W) && unsigned(iy) < unsigned(H);
+    const float v = in ? S(ix, iy, 0, 0) : 0.f;
+    return (in && v == v) ? make_float2(v, 1.f) : make_float2(0.f, 0.f);
+  }
+  float2 w[T::n];
+  weights2<ORDER>(t, w);
+#pragma unroll
+  for (int q = 0; q < T::n; ++q) {
+    w[q].x = (unsigned(ix + q) < unsigned(W)) ? w[q].x : 0.f;
+    w[q].y = (unsigned(iy + q) < unsigned(H)) ? w[q].y : 0.f;
+  }
+  float num = 0.f, f = 0.f;
+#pragma unroll
+  for (int k = 0; k < T::n; ++k) {
+    float row = 0.f, rowf = 0.f;
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) {
+      const float s = S(ix, iy, k, q);
+      const bool ok = s == s;
+      row = fmaf(ok ? w[q].x : 0.f, ok ? s : 0.f, row);
+      rowf += ok ? w[q].x : 0.f;
+    }
+    num = fmaf(w[k].y, row, num);
+    f = fmaf(w[k].y, rowf, f);
+  }
+  if (!(f > 0.f)) return make_float2(0.f, 0.f);
+  return make_float2((f == 1.f) ? num : __fdividef(num, f), f);
+}
+
 // Fallback gather straight from global memory (tiles whose box does not fit, or no TMA).
 template <int ORDER>
 __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int64_t pitch, int W,
-                                             int H, float x, float y, int bx, int by) {
+                                             int H, float x, float y, int bx, int by,
+                                             bool mask = false) {
   auto S = [=](int ix, int iy, int k, int q) -> float {
     const int xx = ix + q, yy = iy + k;
     return (unsigned(xx) < unsigned(W) && unsigned(yy) < unsigned(H))
                ? __ldg(img + int64_t(yy) * pitch + xx)
                : 0.f;
   };
+  if (mask) return interp_pixel_masked<ORDER>(x, y, bx, by, W, H, S);
   return interp_pixel<ORDER, false>(x, y, bx, by, W, H, S);
 }
 
@@ -272,7 +329,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
                                           const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
   if (oy >= Q.h) return;
-  const bool plain = !Q.identity && !Q.tsip && !Q.newton;
+  const bool plain = !Q.identity && !Q.tsip && !Q.newton && !Q.mask;
   if (plain && tb.use_box && tb.interior && ox + kTileW <= Q.w && oy + kTileH <= Q.h) {
     tile_rows_fast<ORDER, IDEG, PAIRS, ACC>(P, Q, a, ox, oy, lane, box, tb);
     return;
@@ -309,9 +366,10 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
         auto SB = [=](int ixa, int iya, int k, int q) -> float {
           return box[(iya + k - by0) * bw + (ixa + q - bx0)];
         };
-        vf = interp_pixel<ORDER, false>(x, y, a.bx, a.by, Q.W, Q.H, SB);
+        vf = Q.mask ? interp_pixel_masked<ORDER>(x, y, a.bx, a.by, Q.W, Q.H, SB)
+                    : interp_pixel<ORDER, false>(x, y, a.bx, a.by, Q.W, Q.H, SB);
       } else {
-        vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by);
+        vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by, Q.mask);
       }
     }
     put_pixel<ACC>(po, pf, vf.x, vf.y);

@@ -341,7 +341,7 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
   if (order < DFR_NEAREST || order > DFR_BICUBIC)
     return fail(DFR_ERR_INVALID_ARG, "order must be DFR_NEAREST, DFR_BILINEAR or DFR_BICUBIC");
-  if (flags & ~(DFR_SPLIT | DFR_EXACT_INVERSE | DFR_NO_TMA))
+  if (flags & ~(DFR_SPLIT | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK))
     return fail(DFR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
   if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative output size");
   if (w > 0 && h > 0) {
@@ -1389,6 +1389,8 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
                                       uint32_t flags, float* grad_src, int64_t gs_pitch,
                                       double* grad_params, void* stream) {
+  if (flags & DFR_NAN_MASK)
+    return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK is not supported by the adjoint");
   FwdPlan P;
   // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
   // split path stages source and gradient boxes by tile, as sized by the plan

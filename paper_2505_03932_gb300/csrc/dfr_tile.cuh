@@ -15,7 +15,7 @@ struct HotPlan {
   static constexpr int NC = (IDEG > 0 && PAIRS) ? poly_ncoef(IDEG) : 1;
   float2 cab[NC];
   int32_t W, H, w, h, x0, y0, box_w, box_h;
-  bool identity, tsip, newton, use_tma;
+  bool identity, tsip, newton, use_tma, mask;
   int64_t out_pitch;
   float* out;
   float* fp;
@@ -40,6 +40,7 @@ __device__ __forceinline__ void load_hot(const FwdPlan& P, HotPlan<IDEG, PAIRS>&
   Q.tsip = P.tsip_deg > 0;
   Q.newton = plan_newton(P);
   Q.use_tma = P.use_tma != 0;
+  Q.mask = (P.flags & DFR_NAN_MASK) != 0;
   Q.out_pitch = P.out_pitch;
   Q.out = P.out;
   Q.fp = P.fp;

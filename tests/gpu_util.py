@@ -34,29 +34,35 @@ def to_dev(img):
     return torch().from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
 
 
-def gpu(src, tgt, img_d, order, precision, bbox=None, exact=False, tma=True):
+def gpu(src, tgt, img_d, order, precision, bbox=None, exact=False, tma=True, nan_mask=False):
     """GPU value, footprint and emitted source coordinates (numpy)."""
     val, fp, cr = dfr().reproject(img_d, src, tgt, bbox=bbox, order=order, precision=precision,
-                                  exact_inverse=exact, coords=True, tma=tma)
+                                  exact_inverse=exact, coords=True, tma=tma, nan_mask=nan_mask)
     torch().cuda.synchronize()
     dfr().device_status()
     return val.cpu().numpy(), fp.cpu().numpy(), cr.cpu().numpy()
 
 
-def value_check(img, order, val, fp, cr, precision):
-    """Oracle interpolation at the GPU's own coordinates; returns max normalised error."""
+def value_check(img, order, val, fp, cr, precision, nan_mask=False):
+    """Oracle interpolation at the GPU's own coordinates; returns max normalised error.
+
+    With nan_mask the remaining weight F can fall below the 0.25 floor of the unmasked case
+    (signed bicubic weights), and FP32 rounding of the weighted sum is divided by F: the error
+    is normalised by max(1, 0.25 / F) as well."""
     x = cr[..., 0].ravel()
     y = cr[..., 1].ravel()
     ok = np.isfinite(x) & np.isfinite(y)
     ov, ofp = OI.interpolate(img, np.where(ok, x, np.nan), np.where(ok, y, np.nan),
                              OR.ORDERS[order] if isinstance(order, str) else order, valid=ok,
-                             use_snap=(precision == "fp64"))
+                             use_snap=(precision == "fp64"), nan_mask=nan_mask)
     g = val.ravel().astype(np.float64)
     gf = fp.ravel().astype(np.float64)
     # coverage decisions are taken in the same precision on both sides: they must agree
     assert np.array_equal(gf != 0, ofp != 0), "coverage differs at %d pixels" % int(
         np.sum((gf != 0) != (ofp != 0)))
     err = np.abs(g - ov) / np.maximum(np.abs(ov), 1.0)
+    if nan_mask:
+        err = err / np.maximum(1.0, 0.25 / np.where(ofp > 0, ofp, 1.0))
     ferr = np.abs(gf - ofp)
     return float(err.max(initial=0.0)), float(ferr.max(initial=0.0))
 

@@ -229,3 +229,10 @@ def test_header_lonpole_folded_into_cd_maps_like_the_oracle(dfr):
         u_o, v_o, ok_o = OW.world_to_intermediate(o, ra_o, dec_o)
         assert np.array_equal(ok_c, ok_o)
         assert np.abs(u_c - u_o).max() < 1e-9 and np.abs(v_c - v_o).max() < 1e-9
+
+
+def test_adjoint_refuses_the_nan_mask_flag(dfr):
+    L = dfr.lib()
+    rc = L.dfr_reproject_backward(None, None, None, 0, None, 0, 0, 0, 0, 0, 1,
+                                  dfr.SPLIT | dfr.NAN_MASK, None, 0, None, None)
+    assert rc == -1 and "NAN_MASK" in L.dfr_last_error().decode()

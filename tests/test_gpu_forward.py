@@ -235,3 +235,32 @@ def test_legacy_header_keywords_lonpole_crota2(precision):
     e, fe = value_check(img, "bicubic", val, fp, cr, precision)
     assert e <= VALUE_RTOL and fe <= 1e-6
     assert (fp > 0).mean() > 0.5
+
+
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_nan_masked_source(order, precision):
+    """DFR_NAN_MASK: NaN source pixels (scattered, plus a 9x6 block) take no weight; the oracle's
+    masked interpolation at the GPU's coordinates matches value and footprint (coverage too).
+    Without the flag the NaN reach the output; the batch path equals the single call."""
+    src, tgt, img = _small_sip(w=400, h=300, seed=13)
+    rng = synth.rng_for(14)
+    holed = img.copy()
+    holed[rng.integers(0, 300, 600), rng.integers(0, 400, 600)] = np.nan
+    holed[120:126, 200:209] = np.nan
+    d = to_dev(holed)
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    val, fp, cr = gpu(src, tgt, d, order, precision, bbox, nan_mask=True)
+    assert np.isfinite(val).all() and np.isfinite(fp).all()
+    e, fe = value_check(holed, order, val, fp, cr, precision, nan_mask=True)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    v1, f1, _ = gpu(src, tgt, to_dev(img), order, precision, bbox)
+    if order == "nearest":
+        assert ((f1 > 0) & (fp == 0)).sum() > 100  # pixels on holes become uncovered
+    else:
+        assert ((fp > 0) & (fp < f1)).sum() > 100  # pixels next to holes keep a partial weight
+    v0, _ = dfr().reproject(d, src, tgt, bbox=bbox, order=order, precision=precision)
+    assert torch().isnan(v0).any()
+    vb, fb = dfr().reproject_batch([d], [src], tgt, [bbox], order=order, precision=precision,
+                                   nan_mask=True)
+    assert np.array_equal(vb[0].cpu().numpy(), val) and np.array_equal(fb[0].cpu().numpy(), fp)

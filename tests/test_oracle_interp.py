@@ -184,3 +184,48 @@ def test_target_bbox_contains_covered_pixels():
     ys, xs = np.nonzero(fp)
     assert xs.min() >= x0 and xs.max() < x0 + w and ys.min() >= y0 and ys.max() < y0 + h
     assert w <= 512 + 20 and h <= 512 + 20
+
+
+def test_nan_mask_pins():
+    """NaN-masked interpolation: (1) an image without NaN gives the unmasked result bit for bit;
+    (2) bilinear next to one NaN tap equals the renormalised average of the other three taps,
+    worked by hand; (3) a constant image with NaN holes interpolates to the constant wherever
+    anything is left, and nearest on a NaN pixel is uncovered; (4) the footprint at an interior
+    point is one minus the weight of the NaN taps."""
+    rng = np.random.default_rng(3)
+    img = rng.standard_normal((20, 24))
+    x = rng.uniform(-0.5, 23.5, 300)
+    y = rng.uniform(-0.5, 19.5, 300)
+    for order in (I.NEAREST, I.BILINEAR, I.BICUBIC):
+        a = I.interpolate(img, x, y, order)
+        b = I.interpolate(img, x, y, order, nan_mask=True)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    holed = img.copy()
+    holed[5, 7] = np.nan
+    # bilinear at (7.25, 4.5): taps (7,4) (8,4) (7,5) (8,5) with weights .375 .125 .375 .125
+    v, f = I.interpolate(holed, np.array([7.25]), np.array([4.5]), I.BILINEAR, nan_mask=True)
+    w = {(4, 7): 0.375, (4, 8): 0.125, (5, 8): 0.125}
+    expect = sum(wt * holed[r, c] for (r, c), wt in w.items()) / 0.625
+    assert abs(f[0] - 0.625) < 1e-15 and abs(v[0] - expect) < 1e-14
+    const = np.full((20, 24), 2.5)
+    const[rng.integers(0, 20, 40), rng.integers(0, 24, 40)] = np.nan
+    for order in (I.BILINEAR, I.BICUBIC):
+        v, f = I.interpolate(const, x, y, order, nan_mask=True)
+        assert np.all(np.abs(v[f > 0] - 2.5) < 1e-12)
+    v, f = I.interpolate(holed, np.array([7.2]), np.array([5.1]), I.NEAREST, nan_mask=True)
+    assert f[0] == 0.0 and v[0] == 0.0
+    v, f = I.interpolate(holed, np.array([6.6]), np.array([5.0]), I.BICUBIC, nan_mask=True)
+    ix, wx = I.taps_1d(np.array([6.6]), I.BICUBIC, -0.5)
+    wnan = wx[7 - ix[0], 0] * 1.0  # y = 5 exactly: the row weight of row 5 is 1
+    assert abs(f[0] - (1.0 - wnan)) < 1e-14
+
+
+def test_nan_mask_nonpositive_remaining_weight_is_uncovered():
+    """Bicubic at t = 1/2 in x: weights (-1/16, 9/16, 9/16, -1/16). With both central columns
+    missing the remaining weight is -1/8 < 0: the pixel is uncovered (value and footprint 0)."""
+    img = np.arange(8 * 8, dtype=np.float64).reshape(8, 8)
+    img[:, 3:5] = np.nan
+    v, f = I.interpolate(img, np.array([3.5]), np.array([3.0]), I.BICUBIC, nan_mask=True)
+    assert v[0] == 0.0 and f[0] == 0.0
+    v, f = I.interpolate(img, np.array([3.5]), np.array([3.0]), I.BILINEAR, nan_mask=True)
+    assert v[0] == 0.0 and f[0] == 0.0  # both bilinear taps missing
