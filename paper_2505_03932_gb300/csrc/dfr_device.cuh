@@ -323,6 +323,25 @@ struct Anchor {
   float tu, tv, tA, tB;  // target SIP argument and value at the anchor (FP32)
 };
 
+// Target forward SIP (A, B) at (u, v) in FP32 at the plan's degree: by the runtime loop, or
+// (UNROLL, for the hot rows of target-SIP kernels) degrees 2-5 unrolled. The FMA sequence is the
+// same either way, so the results are equal bits.
+template <bool UNROLL = false>
+__device__ __forceinline__ void tsip_pair(const FwdPlan& P, float u, float v, float& fa,
+                                          float& fb) {
+  if (!UNROLL) {
+    horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, u, v, fa, fb);
+    return;
+  }
+  switch (P.tsip_deg) {
+    case 2: horner_pair<2, float>(P.tsip_f[0], P.tsip_f[1], u, v, fa, fb); break;
+    case 3: horner_pair<3, float>(P.tsip_f[0], P.tsip_f[1], u, v, fa, fb); break;
+    case 4: horner_pair<4, float>(P.tsip_f[0], P.tsip_f[1], u, v, fa, fb); break;
+    case 5: horner_pair<5, float>(P.tsip_f[0], P.tsip_f[1], u, v, fa, fb); break;
+    default: horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, u, v, fa, fb); break;
+  }
+}
+
 __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
   a.ax = ax;
   a.ay = ay;
@@ -341,8 +360,8 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
   }
   // FP64 only where absolute positions need it: the homography at the anchor and the anchor's
   // source position; the local expansion coefficients follow in FP32
-  const double u = double(ax) - P.crpix_t[0];
-  const double v = double(ay) - P.crpix_t[1];
+  const double u = __dsub_rn(double(ax), P.crpix_t[0]);
+  const double v = __dsub_rn(double(ay), P.crpix_t[1]);
   double p = u, q = v;
   a.tu = float(u);
   a.tv = float(v);
@@ -350,10 +369,10 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
   if (P.tsip_deg > 0) {
     double fa, fb;
     horner_pair_rt<double>(P.tsip_d[0], P.tsip_d[1], P.tsip_deg, u, v, fa, fb);
-    p += fa;
-    q += fb;
+    p = __dadd_rn(p, fa);
+    q = __dadd_rn(q, fb);
     float ga, gb;
-    horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, a.tu, a.tv, ga, gb);
+    tsip_pair(P, a.tu, a.tv, ga, gb);
     a.tA = ga;
     a.tB = gb;
   }
@@ -364,7 +383,9 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
   double r = double(__frcp_rn(float(h2)));
   r = fma(r, fma(-h2, r, 1.0), r);
   r = fma(r, fma(-h2, r, 1.0), r);
-  const double U0 = h0 * r, V0 = h1 * r;
+  // explicit roundings (no contraction of a product into a later sum: every kernel that builds
+  // anchors must get the same bits)
+  const double U0 = __dmul_rn(h0, r), V0 = __dmul_rn(h1, r);
   const float U0f = float(U0), V0f = float(V0);
   const float g20 = float(P.G[2][0]), g21 = float(P.G[2][1]);
   a.a0 = fmaf(-U0f, g20, float(P.G[0][0]));
@@ -376,13 +397,13 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
   a.h2 = float(h2);
   a.U0 = U0f;
   a.V0 = V0f;
-  const double X0 = U0 + P.crpix_s[0], Y0 = V0 + P.crpix_s[1];
+  const double X0 = __dadd_rn(U0, P.crpix_s[0]), Y0 = __dadd_rn(V0, P.crpix_s[1]);
   const double fx = floor(X0), fy = floor(Y0);
   const bool finite = isfinite(X0) && isfinite(Y0) && fabs(X0) < 1e9 && fabs(Y0) < 1e9;
   a.bx = finite ? int32_t(fx) : 0;
   a.by = finite ? int32_t(fy) : 0;
-  a.f0x = finite ? float(X0 - fx) : 0.f;
-  a.f0y = finite ? float(Y0 - fy) : 0.f;
+  a.f0x = finite ? float(__dsub_rn(X0, fx)) : 0.f;
+  a.f0y = finite ? float(__dsub_rn(Y0, fy)) : 0.f;
   if (!finite || !(h2 > 0.0)) a.h2 = -1.f;  // the whole cell is treated as uncovered
 }
 
@@ -403,9 +424,9 @@ __device__ __forceinline__ int cell_anchor_y(const FwdPlan& P, int gy) {
 // arrays; IDEG == 0: no inverse polynomial). All forms run the same FMA sequence, so they
 // give the same bits. The rarely used target-SIP and Newton branches read the plan P; the
 // Newton step's forward SIP has degree FDEG (the plan's padded degree) or, with FDEG < 0, the
-// runtime degree.
+// runtime degree; TSIP_UNROLL selects the unrolled target-SIP evaluation (same bits).
 // geo (nullable) receives (du, dv, eu, ev) for the adjoint.
-template <int IDEG, bool PAIRS = true, int FDEG = -1>
+template <int IDEG, bool PAIRS = true, int FDEG = -1, bool TSIP_UNROLL = false>
 __device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2* cab,
                                                   bool identity, bool tsip, bool newton,
                                                   const Anchor& a, float dx, float dy, float& xr,
@@ -419,56 +440,66 @@ __device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2
     }
     return true;
   }
+  // Every operation is an explicit rounding (fmaf, __fmul_rn, __fadd_rn, ...): the compiler
+  // may not contract a product into a later sum, so every kernel that evaluates this (forward
+  // fast and general rows, coordinate output, adjoint) produces the same bits.
   float dp = dx, dq = dy;
   if (tsip) {
     float fa, fb;
-    horner_pair_rt<float>(P.tsip_f[0], P.tsip_f[1], P.tsip_deg, a.tu + dx, a.tv + dy, fa, fb);
-    dp = dx + (fa - a.tA);
-    dq = dy + (fb - a.tB);
+    tsip_pair<TSIP_UNROLL>(P, __fadd_rn(a.tu, dx), __fadd_rn(a.tv, dy), fa, fb);
+    dp = __fadd_rn(dx, __fsub_rn(fa, a.tA));
+    dq = __fadd_rn(dy, __fsub_rn(fb, a.tB));
   }
-  const float nu = fmaf(a.a0, dp, a.a1 * dq);
-  const float nv = fmaf(a.b0, dp, a.b1 * dq);
+  const float nu = fmaf(a.a0, dp, __fmul_rn(a.a1, dq));
+  const float nv = fmaf(a.b0, dp, __fmul_rn(a.b1, dq));
   const float den = fmaf(a.g20, dp, fmaf(a.g21, dq, a.h2));
   const float rcp = __fdividef(1.f, den);
-  float du = nu * rcp, dv = nv * rcp;
-  float eu = du, ev = dv;
+  // (du, dv) = (nu, nv) / den, fused into each use: U = U0 + du, the position f0 + (ga + du)
+  const float Uq = fmaf(nu, rcp, a.U0), Vq = fmaf(nv, rcp, a.V0);
+  float ga = 0.f, gb = 0.f;  // inverse SIP AP/BP at (U, V)
   if (IDEG > 0 && PAIRS) {
-    const float2 g = horner_pair2<(IDEG > 0 ? IDEG : 1)>(cab, a.U0 + du, a.V0 + dv);
-    eu = du + g.x;
-    ev = dv + g.y;
+    const float2 g = horner_pair2<(IDEG > 0 ? IDEG : 1)>(cab, Uq, Vq);
+    ga = g.x;
+    gb = g.y;
   } else if (IDEG > 0) {
     // scalar FMAs reading the plan directly (constant-bank operands for a kernel parameter)
-    float ga, gb;
-    horner_pair<(IDEG > 0 ? IDEG : 1), float>(P.isip_f[0], P.isip_f[1], a.U0 + du, a.V0 + dv,
-                                              ga, gb);
-    eu = du + ga;
-    ev = dv + gb;
+    horner_pair<(IDEG > 0 ? IDEG : 1), float>(P.isip_f[0], P.isip_f[1], Uq, Vq, ga, gb);
   } else if (IDEG < 0 && P.isip_deg > 0) {
-    float ga, gb;
-    horner_pair_rt<float>(P.isip_f[0], P.isip_f[1], P.isip_deg, a.U0 + du, a.V0 + dv, ga, gb);
-    eu = du + ga;
-    ev = dv + gb;
+    horner_pair_rt<float>(P.isip_f[0], P.isip_f[1], P.isip_deg, Uq, Vq, ga, gb);
   }
-  if (newton) {
-    // Newton on e = u - U0: e + A(U0 + e) = du, started from the AP/BP estimate.
-    for (int it = 0; it < P.newton_iters; ++it) {
-      float A, Au, Av, B, Bu, Bv;
-      poly_grad<FDEG, float>(P.fsip_f[0], P.fsip_deg, a.U0 + eu, a.V0 + ev, A, Au, Av);
-      poly_grad<FDEG, float>(P.fsip_f[1], P.fsip_deg, a.U0 + eu, a.V0 + ev, B, Bu, Bv);
-      const float ru = (eu - du) + A, rv = (ev - dv) + B;
-      const float j00 = 1.f + Au, j11 = 1.f + Bv;
-      const float det = fmaf(j00, j11, -Av * Bu);
-      const float inv = __fdividef(1.f, det);
-      eu -= fmaf(j11, ru, -Av * rv) * inv;
-      ev -= fmaf(j00, rv, -Bu * ru) * inv;
+  if (!newton) {
+    xr = fmaf(nu, rcp, __fadd_rn(a.f0x, ga));
+    yr = fmaf(nv, rcp, __fadd_rn(a.f0y, gb));
+    if (geo) {
+      const float du = __fmul_rn(nu, rcp), dv = __fmul_rn(nv, rcp);
+      geo[0] = du;  // source intermediate offsets before the inverse SIP, relative to (U0, V0)
+      geo[1] = dv;
+      geo[2] = __fadd_rn(du, ga);  // ... and after it
+      geo[3] = __fadd_rn(dv, gb);
     }
+    return den > 0.f && a.h2 > 0.f;
   }
-  xr = a.f0x + eu;
-  yr = a.f0y + ev;
+  const float du = __fmul_rn(nu, rcp), dv = __fmul_rn(nv, rcp);
+  float eu = __fadd_rn(du, ga), ev = __fadd_rn(dv, gb);
+  // Newton on e = u - U0: e + A(U0 + e) = du, started from the AP/BP estimate.
+  for (int it = 0; it < P.newton_iters; ++it) {
+    float A, Au, Av, B, Bu, Bv;
+    const float Ue = __fadd_rn(a.U0, eu), Ve = __fadd_rn(a.V0, ev);
+    poly_grad<FDEG, float>(P.fsip_f[0], P.fsip_deg, Ue, Ve, A, Au, Av);
+    poly_grad<FDEG, float>(P.fsip_f[1], P.fsip_deg, Ue, Ve, B, Bu, Bv);
+    const float ru = __fadd_rn(__fsub_rn(eu, du), A), rv = __fadd_rn(__fsub_rn(ev, dv), B);
+    const float j00 = __fadd_rn(1.f, Au), j11 = __fadd_rn(1.f, Bv);
+    const float det = fmaf(j00, j11, -__fmul_rn(Av, Bu));
+    const float inv = __fdividef(1.f, det);
+    eu = __fsub_rn(eu, __fmul_rn(fmaf(j11, ru, -__fmul_rn(Av, rv)), inv));
+    ev = __fsub_rn(ev, __fmul_rn(fmaf(j00, rv, -__fmul_rn(Bu, ru)), inv));
+  }
+  xr = __fadd_rn(a.f0x, eu);
+  yr = __fadd_rn(a.f0y, ev);
   if (geo) {
-    geo[0] = du;  // source intermediate offsets before the inverse SIP, relative to (U0, V0)
+    geo[0] = du;
     geo[1] = dv;
-    geo[2] = eu;  // ... and after it
+    geo[2] = eu;
     geo[3] = ev;
   }
   return den > 0.f && a.h2 > 0.f;

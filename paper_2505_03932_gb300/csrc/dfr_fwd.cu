@@ -72,6 +72,7 @@ static const void* kernel_for_order(bool split, bool batch, int ideg) {
 static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
   if (p0.flags & kFlagAccumulate) return batch ? nullptr : coadd_kernel(p0);
   const bool split = (p0.flags & DFR_SPLIT) != 0;
+  if (split && !batch && p0.tsip_deg > 0) return tsip_kernel(p0);
   switch (p0.order) {
     case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, batch, p0.isip_deg);
     case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, batch, p0.isip_deg);

@@ -227,6 +227,17 @@ __device__ __forceinline__ float2 interp_pixel_masked(float x, float y, int bx, 
   return make_float2((f == 1.f) ? num : __fdividef(num, f), f);
 }
 
+// Masked gather from a warp's shared-memory box whose origin is (bx0, by0), width bw. Not
+// inlined: the masked path is rare, and its registers stay out of the kernels' hot rows.
+template <int ORDER>
+__device__ __noinline__ float2 gather_box_masked(const float* box, int bw, int bx0, int by0,
+                                                 int W, int H, float x, float y, int bx, int by) {
+  auto SB = [=](int ixa, int iya, int k, int q) -> float {
+    return box[(iya + k - by0) * bw + (ixa + q - bx0)];
+  };
+  return interp_pixel_masked<ORDER>(x, y, bx, by, W, H, SB);
+}
+
 // Fallback gather straight from global memory (tiles whose box does not fit, or no TMA).
 template <int ORDER>
 __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int64_t pitch, int W,
@@ -245,10 +256,10 @@ __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int6
 // Rows of one tile: per pixel the split coordinates, coverage, then the gather from the box
 // (fast when the tile is interior) or from global memory.
 // Fast rows: the tile lies inside the bounding box, its widened source extent inside the image
-// and inside the loaded box, and the plan has no target SIP, Newton inverse or identity. No
+// and inside the loaded box, and the plan has no Newton inverse, NaN mask or identity. No
 // per-pixel branch: taps are read from the box at clamped positions and the rare pixel whose
 // taps leave the box (the curvature margin was too small) is redone from global memory.
-template <int ORDER, int IDEG, bool PAIRS, bool ACC>
+template <int ORDER, int IDEG, bool PAIRS, bool ACC, bool TSIP>
 __device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
                                                const Anchor& a, int ox, int oy, int lane,
                                                const float* box, const TileBox& tb) {
@@ -268,7 +279,8 @@ __device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<I
 #pragma unroll 2  // measured: full unrolling costs more in instruction fetch than it saves
   for (int r = 0; r < kTileH; ++r) {
     float x, y;
-    const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx, dy, x, y);
+    const bool ok = split_coords_core<IDEG, PAIRS, -1, TSIP>(P, Q.cab, false, TSIP, false, a, dx,
+                                                             dy, x, y);
     const float flx = floorf(x), fly = floorf(y);
     const float2 t = make_float2(x - flx, y - fly);
     int ux = int(flx) + ux0, uy = int(fly) + uy0;
@@ -310,7 +322,7 @@ __device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<I
     for (int r = 0; r < kTileH; ++r) {
       if (!((bad >> r) & 1u)) continue;
       float x, y;
-      const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, false, false, a, dx,
+      const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, TSIP, false, a, dx,
                                                      float(Q.y0 + oy - a.ay) + float(r), x, y);
       float2 vf = make_float2(0.f, 0.f);
       if (ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi)
@@ -323,15 +335,17 @@ __device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<I
 
 // General rows: per pixel the split coordinates, coverage, then the gather from the box (when
 // its taps are in the box) or from global memory.
-template <int ORDER, int IDEG, bool PAIRS, bool ACC>
+template <int ORDER, int IDEG, bool PAIRS, bool ACC, bool TSIP>
 __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
                                           const Anchor& a, int ox, int oy, int lane,
                                           const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
   if (oy >= Q.h) return;
-  const bool plain = !Q.identity && !Q.tsip && !Q.newton && !Q.mask;
+  // (the fast rows of a TSIP instantiation serve plans with target SIP, the others plans
+  // without; the remaining plans take the general rows)
+  const bool plain = !Q.identity && !Q.newton && !Q.mask && Q.tsip == TSIP;
   if (plain && tb.use_box && tb.interior && ox + kTileW <= Q.w && oy + kTileH <= Q.h) {
-    tile_rows_fast<ORDER, IDEG, PAIRS, ACC>(P, Q, a, ox, oy, lane, box, tb);
+    tile_rows_fast<ORDER, IDEG, PAIRS, ACC, TSIP>(P, Q, a, ox, oy, lane, box, tb);
     return;
   }
   const int gx = ox + lane;
@@ -366,7 +380,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
         auto SB = [=](int ixa, int iya, int k, int q) -> float {
           return box[(iya + k - by0) * bw + (ixa + q - bx0)];
         };
-        vf = Q.mask ? interp_pixel_masked<ORDER>(x, y, a.bx, a.by, Q.W, Q.H, SB)
+        vf = Q.mask ? gather_box_masked<ORDER>(box, bw, bx0, by0, Q.W, Q.H, x, y, a.bx, a.by)
                     : interp_pixel<ORDER, false>(x, y, a.bx, a.by, Q.W, Q.H, SB);
       } else {
         vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by, Q.mask);
@@ -382,8 +396,11 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
 // CTAs (of kWarps warps) per SM the register budget targets: 6 (80 registers) for single-frame
 // launches, whose inverse-SIP coefficients are constant-bank operands; 4 (128) for batch
 // launches, which hold them in registers.
-// Accumulating (co-add) launches hold the read-modify-write operands as well: 5 (96 registers).
-constexpr int split_min_blocks(bool batch, bool acc) { return batch ? 4 : (acc ? 5 : 6); }
+// Accumulating (co-add) launches hold the read-modify-write operands as well, and target-SIP
+// launches the target polynomial: 5 (96 registers).
+constexpr int split_min_blocks(bool batch, bool acc, bool tsip) {
+  return batch ? 4 : ((acc || tsip) ? 5 : 6);
+}
 
 __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
   int lo = 0, hi = L.nframes - 1;
@@ -420,8 +437,8 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
 // Work unit: kCellsPerCta consecutive 32x32 anchor cells. Warp 0 computes their FP64 anchors
 // (one lane per cell), then each warp processes the 4 tiles of each of its kCellsPerWarp cells,
 // requesting the source box of the next tile before gathering the current one.
-template <int ORDER, int IDEG, bool BATCH, bool ACC>
-__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC)) fwd_split_kernel(
+template <int ORDER, int IDEG, bool BATCH, bool ACC, bool TSIP = false>
+__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP)) fwd_split_kernel(
     const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
   extern __shared__ __align__(128) float box_raw[];
   __shared__ Anchor s_anc[kCellsPerCta];
@@ -477,9 +494,9 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC)) fwd
         load_hot(P, Q);
         const Anchor a = s_anc[j0];
         const int cell = s_cell[j0];
-        cur = tile_box<ORDER, IDEG, BATCH>(P, Q, a, (cell % P.cells_x) * kCellW,
-                                           (cell / P.cells_x) * kCellH, lane, box, &bar[0],
-                                           batch);
+        cur = tile_box<ORDER, IDEG, BATCH, TSIP>(P, Q, a, (cell % P.cells_x) * kCellW,
+                                                 (cell / P.cells_x) * kCellH, lane, box, &bar[0],
+                                                 batch);
         prefetch_sums<ACC>(Q, (cell % P.cells_x) * kCellW, (cell / P.cells_x) * kCellH, lane);
       }
       for (int t = 0; t < nt; ++t) {
@@ -493,9 +510,10 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC)) fwd
           load_hot(Pn, Qn);
           const Anchor an = s_anc[jn];
           const int celln = s_cell[jn];
-          nxt = tile_box<ORDER, IDEG, BATCH>(Pn, Qn, an, (celln % Pn.cells_x) * kCellW,
-                                             (celln / Pn.cells_x) * kCellH + kn * kTileH, lane,
-                                             box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch);
+          nxt = tile_box<ORDER, IDEG, BATCH, TSIP>(
+              Pn, Qn, an, (celln % Pn.cells_x) * kCellW,
+              (celln / Pn.cells_x) * kCellH + kn * kTileH, lane, box + (b ^ 1) * L.box_floats,
+              &bar[b ^ 1], batch);
           prefetch_sums<ACC>(Qn, (celln % Pn.cells_x) * kCellW,
                              (celln / Pn.cells_x) * kCellH + kn * kTileH, lane);
         }
@@ -509,7 +527,7 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC)) fwd
           if (!mbar_wait(&bar[b], (phase >> b) & 1u)) cur.use_box = false;  // timed out
           phase ^= 1u << b;
         }
-        tile_rows<ORDER, IDEG, BATCH, ACC>(P, Q, a, (cell % P.cells_x) * kCellW,
+        tile_rows<ORDER, IDEG, BATCH, ACC, TSIP>(P, Q, a, (cell % P.cells_x) * kCellW,
                                       (cell / P.cells_x) * kCellH + k * kTileH, lane,
                                       box + b * L.box_floats, cur);
         cur = nxt;

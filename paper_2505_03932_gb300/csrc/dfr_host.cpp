@@ -1001,12 +1001,14 @@ int dfr_device_status(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   e = read_and_clear_status_bwd(&b, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
-  int32_t c = 0, d = 0;
+  int32_t c = 0, d = 0, t = 0;
   e = read_and_clear_status_bwd_tile(&c, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   e = read_and_clear_status_coadd(&d, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
-  const int32_t s = a | b | c | d;
+  e = read_and_clear_status_tsip(&t, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  const int32_t s = a | b | c | d | t;
   if (s & kStatusTimeout) return fail(DFR_ERR_TIMEOUT, "a bounded device wait gave up");
   if (s & kStatusCheck) return fail(DFR_ERR_DEVICE, "a kernel reported a failed check");
   return DFR_OK;

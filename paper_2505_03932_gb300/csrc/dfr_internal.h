@@ -128,6 +128,7 @@ cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd_tile(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_coadd(int32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_status_tsip(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
@@ -135,6 +136,7 @@ int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats);
 int backward_threads_for(const FwdPlan& p0, int fd);
 const void* backward_tile_kernel(int order, int ideg, int fd);  // dfr_bwd_tile.cu
 const void* coadd_kernel(const FwdPlan& p0);                      // dfr_coadd.cu
+const void* tsip_kernel(const FwdPlan& p0);                       // dfr_fwd_tsip.cu
 cudaError_t launch_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch,
                                    int32_t w, int32_t h, float min_weight, float* mean,
                                    int64_t mean_pitch, cudaStream_t s);

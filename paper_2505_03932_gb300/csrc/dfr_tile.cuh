@@ -57,7 +57,7 @@ struct TileBox {
   bool empty;        // the widened extent misses the image: nothing in the tile is covered
 };
 
-template <int ORDER, int IDEG, bool PAIRS>
+template <int ORDER, int IDEG, bool PAIRS, bool TSIP_UNROLL = false>
 __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
                                             const Anchor& a, int ox, int oy, int lane,
                                             float* box, uint64_t* bar, bool map_in_gmem,
@@ -76,9 +76,9 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HotPlan<IDEG
   float x = 0.f, y = 0.f;
   bool ok = true;
   if (lane < 4)
-    ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a,
-                                        float(Q.x0 + ox + cx - a.ax),
-                                        float(Q.y0 + oy + cy - a.ay), x, y);
+    ok = split_coords_core<IDEG, PAIRS, -1, TSIP_UNROLL>(
+        P, Q.cab, Q.identity, Q.tsip, Q.newton, a, float(Q.x0 + ox + cx - a.ax),
+        float(Q.y0 + oy + cy - a.ay), x, y);
   ok = ok && fabsf(x) < 1e7f && fabsf(y) < 1e7f;
   if (!__all_sync(0xffffffffu, ok)) return tb;  // corners undefined: gather per pixel
   const int fx = int(floorf(x)), fy = int(floorf(y));

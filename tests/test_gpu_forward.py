@@ -121,8 +121,26 @@ def test_linear_ramp_bilinear_and_quadratic_bicubic():
             assert np.abs(val - exact)[inner].max() <= 1e-6 * np.abs(img).max() + 4e-7 * 8
 
 
-def test_tma_and_direct_gather_agree_bitwise():
-    src, tgt, img = _small_sip()
+def _far_pair(target_sip):
+    """Different tangent points (a projective map with a live denominator), rotation and scale
+    change, optionally a SIP target grid."""
+    rng = synth.rng_for(99)
+    src = synth.add_sip(synth.tan_wcs(500, 400, crval=(150.0, 30.0)), 3, 1e-6, rng)
+    src, _ = OW.with_inverse_sip(src, 4)
+    tgt = synth.tan_wcs(520, 380, crval=(150.05, 30.04), rho_deg=-2.0, scale_arcsec=2.7)
+    if target_sip:
+        tgt = synth.add_sip(tgt, 2, 1e-6, rng)
+    return src, tgt, synth.sky_image(500, 400, 40, rng)
+
+
+@pytest.mark.parametrize("case", ["small_sip", "far_tangent", "far_tangent_target_sip"])
+def test_tma_and_direct_gather_agree_bitwise(case):
+    """The TMA-staged rows (interior fast path included) and the direct global-memory gather run
+    the same arithmetic: values, footprints and emitted coordinates are equal bit for bit."""
+    if case == "small_sip":
+        src, tgt, img = _small_sip()
+    else:
+        src, tgt, img = _far_pair(case.endswith("target_sip"))
     bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
     for order in ("nearest", "bilinear", "bicubic"):
         a = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=True)
