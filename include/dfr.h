@@ -54,6 +54,7 @@ extern "C" {
 #define DFR_NEAREST  0
 #define DFR_BILINEAR 1
 #define DFR_BICUBIC  2   /* Keys cubic convolution, a = -0.5 */
+#define DFR_LANCZOS3 3   /* Lanczos-3 (6x6 taps, weights normalised per axis); forward only */
 
 /* flags */
 #define DFR_FP64           0u  /* all-FP64 per pixel: the printed formulas, with libm trig   */
@@ -122,7 +123,7 @@ int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]);
 /* Reproject one source image onto a bounding box of the target grid (Sec. 3.1 steps 1-3,
  * Sec. 3.2). src_img: device, src->naxis[1] rows, row stride src_pitch. out: device,
  * out_h rows of out_w values, row stride out_pitch. footprint: device, same layout, nullable.
- * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC. flags: DFR_FP64 or DFR_SPLIT, optionally
+ * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC / DFR_LANCZOS3. flags: DFR_FP64 or DFR_SPLIT, optionally
  * | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK. Without DFR_NAN_MASK, NaN source pixels
  * propagate into the values they touch. coords_out (nullable, device): 2*out_w*out_h doubles,
  * the source position (x then y per pixel, row-major) exactly as the kernel used it, NaN where

@@ -15,6 +15,9 @@ Readings taken here:
   * bilinear: tent weights (1 - t, t) at floor(x), floor(x) + 1.
   * bicubic: Keys (1981) cubic convolution with parameter a (default -0.5), taps floor(x) - 1
     .. floor(x) + 2, written from its piecewise kernel definition.
+  * lanczos3 (an extension beyond the paper's three schemes): the Lanczos kernel
+    L(d) = sinc(d) sinc(d / 3) for |d| < 3, taps floor(x) - 2 .. floor(x) + 3, weights divided
+    by their sum along each axis (so they sum to 1 and a constant is reproduced).
   * FP64 snapping: a coordinate within 1e-9 px of an integer is taken as that integer (so that
     an identity map returns its input bit for bit despite round-off in the transform).
 """
@@ -22,7 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NEAREST, BILINEAR, BICUBIC = 0, 1, 2
+NEAREST, BILINEAR, BICUBIC, LANCZOS3 = 0, 1, 2, 3
 SNAP_PX = 1e-9
 
 
@@ -35,6 +38,12 @@ def keys_kernel(s, a=-0.5):
     out[m1] = (a + 2.0) * s[m1] ** 3 - (a + 3.0) * s[m1] ** 2 + 1.0
     out[m2] = a * s[m2] ** 3 - 5.0 * a * s[m2] ** 2 + 8.0 * a * s[m2] - 4.0 * a
     return out
+
+
+def lanczos3_kernel(d):
+    """L(d) = sinc(d) sinc(d / 3) for |d| < 3, else 0 (numpy's sinc is sin(pi x) / (pi x))."""
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(np.abs(d) < 3.0, np.sinc(d) * np.sinc(d / 3.0), 0.0)
 
 
 def taps_1d(coord, order, a=-0.5):
@@ -50,6 +59,9 @@ def taps_1d(coord, order, a=-0.5):
         w = np.stack([keys_kernel(t + 1.0, a), keys_kernel(t, a),
                       keys_kernel(1.0 - t, a), keys_kernel(2.0 - t, a)])
         return (i0 - 1).astype(np.int64), w
+    if order == LANCZOS3:
+        w = np.stack([lanczos3_kernel(t + 2.0 - k) for k in range(6)])
+        return (i0 - 2).astype(np.int64), w / w.sum(axis=0)
     raise ValueError("order")
 
 

@@ -14,7 +14,8 @@ import numpy as np
 from . import interp as _interp
 from . import wcs as _wcs
 
-ORDERS = {"nearest": _interp.NEAREST, "bilinear": _interp.BILINEAR, "bicubic": _interp.BICUBIC}
+ORDERS = {"nearest": _interp.NEAREST, "bilinear": _interp.BILINEAR, "bicubic": _interp.BICUBIC,
+          "lanczos3": _interp.LANCZOS3}
 CHUNK = 1 << 20
 
 

@@ -20,13 +20,13 @@ __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
     "coadd", "coadd_normalize", "calculate_reprojection",
-    "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "FP64", "SPLIT",
+    "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "LANCZOS3", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA", "NAN_MASK",
 ]
 
-NEAREST, BILINEAR, BICUBIC = 0, 1, 2
+NEAREST, BILINEAR, BICUBIC, LANCZOS3 = 0, 1, 2, 3
 FP64, SPLIT, EXACT_INVERSE, NO_TMA, NAN_MASK = 0, 1, 2, 4, 8
-ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC}
+ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC, "lanczos3": LANCZOS3}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.environ.get("DFR_LIBRARY") or os.path.join(_HERE, "libdfr.so")
 

@@ -154,6 +154,40 @@ template <int ORDER> struct Taps;
 template <> struct Taps<DFR_NEAREST> { static constexpr int n = 1, lo = 0; };
 template <> struct Taps<DFR_BILINEAR> { static constexpr int n = 2, lo = 0; };
 template <> struct Taps<DFR_BICUBIC> { static constexpr int n = 4, lo = -1; };
+template <> struct Taps<DFR_LANCZOS3> { static constexpr int n = 6, lo = -2; };
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Lanczos-3 (sinc window sinc(d/3), |d| < 3) at the six tap offsets d_k = t + 2 - k, normalised
+// to sum 1. With th = pi t / 3: sin(pi d_k) = (-1)^k sin(pi t) and sin(pi d_k / 3) =
+// sin(th + pi (2 - k) / 3) (angle addition); the common factor 3 sin(pi t) / pi^2 of
+// sinc(d) sinc(d / 3) cancels in the normalisation, leaving w_k proportional to
+// (-1)^k sin(th + pi (2 - k) / 3) / d_k^2. Below t = 1e-12 the weights of t = 0 (1 at the node).
+template <typename T>
+__device__ __forceinline__ void lanczos3_weights(T t, T* w) {
+  if (t < T(1e-12)) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = (k == 2) ? T(1) : T(0);
+    return;
+  }
+  T s, c;
+  sincospi_t(t / T(3), &s, &c);
+  const T h = T(0.86602540378443864676);  // sin(pi / 3)
+  const T a[6] = {fma(c, h, T(-0.5) * s), fma(c, h, T(0.5) * s), s,
+                  fma(-c, h, T(0.5) * s), fma(-c, h, T(-0.5) * s), -s};
+  T sum = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const T d = t + T(2 - k);
+    const T v = ((k & 1) ? -a[k] : a[k]) / (d * d);
+    w[k] = v;
+    sum += v;
+  }
+  const T inv = T(1) / sum;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) w[k] *= inv;
+}
 
 // t = x - floor(x) in [0, 1). Nearest is handled by the caller (index shift when t >= 1/2).
 template <int ORDER, typename T>
@@ -163,6 +197,8 @@ __device__ __forceinline__ void weights(T t, T* w) {
   } else if (ORDER == DFR_BILINEAR) {
     w[0] = T(1) - t;
     w[1] = t;
+  } else if (ORDER == DFR_LANCZOS3) {
+    lanczos3_weights<T>(t, w);
   } else {
     // Keys cubic convolution, a = -0.5, at distances 1+t, t, 1-t, 2-t
     const T s = T(1) - t;
@@ -185,6 +221,12 @@ __device__ __forceinline__ void weights2(float2 t, float2* w) {
   } else if (ORDER == DFR_BILINEAR) {
     w[0] = __fadd2_rn(one, nt);
     w[1] = t;
+  } else if (ORDER == DFR_LANCZOS3) {
+    float wx[6], wy[6];
+    lanczos3_weights<float>(t.x, wx);
+    lanczos3_weights<float>(t.y, wy);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = make_float2(wx[k], wy[k]);
   } else {
     const float2 s = __fadd2_rn(one, nt);
     const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);

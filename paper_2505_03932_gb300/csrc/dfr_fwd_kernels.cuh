@@ -397,9 +397,9 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
 // launches, whose inverse-SIP coefficients are constant-bank operands; 4 (128) for batch
 // launches, which hold them in registers.
 // Accumulating (co-add) launches hold the read-modify-write operands as well, and target-SIP
-// launches the target polynomial: 5 (96 registers).
-constexpr int split_min_blocks(bool batch, bool acc, bool tsip) {
-  return batch ? 4 : ((acc || tsip) ? 5 : 6);
+// launches the target polynomial: 5 (96 registers). Lanczos-3 (36 taps): 4 (128 registers).
+constexpr int split_min_blocks(bool batch, bool acc, bool tsip, int order) {
+  return (batch || order == DFR_LANCZOS3) ? 4 : ((acc || tsip) ? 5 : 6);
 }
 
 __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
 // (one lane per cell), then each warp processes the 4 tiles of each of its kCellsPerWarp cells,
 // requesting the source box of the next tile before gathering the current one.
 template <int ORDER, int IDEG, bool BATCH, bool ACC, bool TSIP = false>
-__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP)) fwd_split_kernel(
+__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP, ORDER)) fwd_split_kernel(
     const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
   extern __shared__ __align__(128) float box_raw[];
   __shared__ Anchor s_anc[kCellsPerCta];

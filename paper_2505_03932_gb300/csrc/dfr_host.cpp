@@ -320,7 +320,7 @@ void size_box(FwdPlan& P) {
   const double A = kTileW - 1, B = kTileH - 1;
   const double dev = (kxx * A * A + 2 * kxy * A * B + kyy * B * B) / 8.0;
   P.box_margin = 1 + int(std::ceil(4.0 * dev));
-  const int ext = (P.order == DFR_BICUBIC) ? 4 : 2;
+  const int ext = (P.order == DFR_LANCZOS3) ? 6 : (P.order == DFR_BICUBIC) ? 4 : 2;
   const double sx = 1.1 * (jxx * (kTileW - 1) + jxy * (kTileH - 1)) + 1.0;
   const double sy = 1.1 * (jyx * (kTileW - 1) + jyy * (kTileH - 1)) + 1.0;
   int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
@@ -339,8 +339,9 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   int rc;
   if ((rc = check_wcs(src, "source")) != DFR_OK) return rc;
   if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
-  if (order < DFR_NEAREST || order > DFR_BICUBIC)
-    return fail(DFR_ERR_INVALID_ARG, "order must be DFR_NEAREST, DFR_BILINEAR or DFR_BICUBIC");
+  if (order < DFR_NEAREST || order > DFR_LANCZOS3)
+    return fail(DFR_ERR_INVALID_ARG,
+                "order must be DFR_NEAREST, DFR_BILINEAR, DFR_BICUBIC or DFR_LANCZOS3");
   if (flags & ~(DFR_SPLIT | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK))
     return fail(DFR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
   if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative output size");
@@ -1393,6 +1394,8 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       double* grad_params, void* stream) {
   if (flags & DFR_NAN_MASK)
     return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK is not supported by the adjoint");
+  if (order == DFR_LANCZOS3)
+    return fail(DFR_ERR_INVALID_ARG, "DFR_LANCZOS3 is not supported by the adjoint");
   FwdPlan P;
   // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
   // split path stages source and gradient boxes by tile, as sized by the plan

@@ -131,7 +131,7 @@ def test_argument_errors_before_any_launch(dfr):
         ctypes.byref(kw.get("s", s)), ctypes.byref(t), kw.get("img", dummy), kw.get("pitch", 64),
         kw.get("out", dummy), None, kw.get("opitch", 64), 0, 0, kw.get("w", 64), kw.get("h", 64),
         kw.get("order", 1), kw.get("flags", 1), None, None)
-    assert call(order=3) == -1
+    assert call(order=4) == -1
     assert call(flags=64) == -1
     assert call(pitch=10) == -1
     assert call(opitch=10) == -1
@@ -236,3 +236,12 @@ def test_adjoint_refuses_the_nan_mask_flag(dfr):
     rc = L.dfr_reproject_backward(None, None, None, 0, None, 0, 0, 0, 0, 0, 1,
                                   dfr.SPLIT | dfr.NAN_MASK, None, 0, None, None)
     assert rc == -1 and "NAN_MASK" in L.dfr_last_error().decode()
+
+
+def test_adjoint_refuses_lanczos3(dfr):
+    L = dfr.lib()
+    s = dfr.to_c(synth.tan_wcs(64, 64))
+    rc = L.dfr_reproject_backward(ctypes.byref(s), ctypes.byref(s), ctypes.c_void_p(16), 64,
+                                  ctypes.c_void_p(16), 64, 0, 0, 64, 64, dfr.LANCZOS3, dfr.SPLIT,
+                                  None, 0, None, None)
+    assert rc == -1 and "LANCZOS3" in L.dfr_last_error().decode()

@@ -64,7 +64,7 @@ def _reference_at_gpu_coords(srcs, imgs, tgt, order, precision):
     return rv, rf, mag, singles
 
 
-@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic", "lanczos3"])
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_coadd_matches_oracle_and_single_frames(order, precision):
     srcs, imgs, tgt = _stack()

@@ -47,7 +47,7 @@ def test_config0_full(precision):
         assert np.abs(fp - ofp).max() <= 1e-6
 
 
-@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic", "lanczos3"])
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_sip_ragged_tiles(order, precision):
     src, tgt, img = _small_sip()
@@ -142,7 +142,7 @@ def test_tma_and_direct_gather_agree_bitwise(case):
     else:
         src, tgt, img = _far_pair(case.endswith("target_sip"))
     bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
-    for order in ("nearest", "bilinear", "bicubic"):
+    for order in ("nearest", "bilinear", "bicubic", "lanczos3"):
         a = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=True)
         b = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=False)
         for u, v in zip(a, b):
@@ -282,3 +282,21 @@ def test_nan_masked_source(order, precision):
     vb, fb = dfr().reproject_batch([d], [src], tgt, [bbox], order=order, precision=precision,
                                    nan_mask=True)
     assert np.array_equal(vb[0].cpu().numpy(), val) and np.array_equal(fb[0].cpu().numpy(), fp)
+
+
+
+def test_lanczos3_identity_and_constant():
+    """Lanczos-3 on the GPU: the identity map returns the image bit for bit (weights 1 at the
+    node), and a constant image is reproduced to FP32 rounding on every covered pixel."""
+    src = synth.tan_wcs(300, 200)
+    img = synth.sky_image(300, 200, 20, synth.rng_for(30))
+    for precision in ("fp64", "split"):
+        v, f = dfr().reproject(to_dev(img), src, src, order="lanczos3", precision=precision)
+        assert np.array_equal(v.cpu().numpy(), img) and bool((f == 1).all())
+    tgt = synth.tan_wcs(320, 210, rho_deg=1.7, crpix=(152.3, 98.9))
+    const = np.full((200, 300), 2.5, np.float32)
+    for precision in ("fp64", "split"):
+        v, f = dfr().reproject(to_dev(const), src, tgt, order="lanczos3", precision=precision)
+        v, f = v.cpu().numpy(), f.cpu().numpy()
+        assert (f > 0).mean() > 0.5
+        assert np.abs(v[f > 0] - 2.5).max() < 1e-5

@@ -229,3 +229,34 @@ def test_nan_mask_nonpositive_remaining_weight_is_uncovered():
     assert v[0] == 0.0 and f[0] == 0.0
     v, f = I.interpolate(img, np.array([3.5]), np.array([3.0]), I.BILINEAR, nan_mask=True)
     assert v[0] == 0.0 and f[0] == 0.0  # both bilinear taps missing
+
+
+def test_lanczos3_pins():
+    """Lanczos-3: closed-form weights at t = 1/2 (sinc(1/2) = 2/pi, sinc(1/6) = 3/pi,
+    sinc(3/2) = -2/(3 pi), sinc(5/2) = 2/(5 pi), sinc(5/6) = 3/(5 pi)), interpolation at the
+    nodes (weights 1 at the node), symmetry w_k(t) = w_{5-k}(1 - t), partition of unity, and a
+    constant image reproduced on every covered pixel."""
+    pi = np.pi
+    L05 = (2 / pi) * (3 / pi)
+    L15 = (-2 / (3 * pi)) * (2 / pi)
+    L25 = (2 / (5 * pi)) * (3 / (5 * pi))
+    raw = np.array([L25, L15, L05, L05, L15, L25])
+    i0, w = I.taps_1d(np.array([4.5]), I.LANCZOS3)
+    assert i0[0] == 2
+    assert np.allclose(w[:, 0], raw / raw.sum(), rtol=0, atol=1e-15)
+    for x in (0.0, 3.0, 7.0):
+        _, w = I.taps_1d(np.array([x]), I.LANCZOS3)
+        assert np.allclose(w[:, 0], [0, 0, 1, 0, 0, 0], rtol=0, atol=1e-15)
+    t = np.linspace(0.01, 0.99, 57)
+    _, w = I.taps_1d(t, I.LANCZOS3)
+    _, wr = I.taps_1d(1.0 - t, I.LANCZOS3)
+    assert np.allclose(w, wr[::-1], rtol=0, atol=1e-14)
+    assert np.allclose(w.sum(axis=0), 1.0, rtol=0, atol=1e-14)
+    rng = np.random.default_rng(11)
+    img = rng.standard_normal((20, 30))
+    xs, ys = np.meshgrid(np.arange(30.0), np.arange(20.0))
+    v, f = I.interpolate(img, xs.ravel(), ys.ravel(), I.LANCZOS3)
+    assert np.allclose(v, img.ravel(), rtol=0, atol=1e-12)
+    v, f = I.interpolate(np.full((20, 30), 1.75), rng.uniform(-0.5, 29.5, 400),
+                         rng.uniform(-0.5, 19.5, 400), I.LANCZOS3)
+    assert np.all(f > 0) and np.abs(v - 1.75).max() < 1e-12
