@@ -459,6 +459,26 @@ def run_extra(args):
         out.append({"workload": "4096^2 SIP3 -> 4096^2 TAN, Lanczos-3, split",
                     "forward_ms": t_f, "forward_mpix_s": 16.777216 / t_f * 1e3,
                     "roofline_frac_hbm": (12 * 16777216 / (t_f * 1e-3)) / 1e9 / _peaks()[0]})
+    if args.workload in ("bspline4096", "all"):
+        # the bench frame with the cubic B-spline: prefilter once, then reproject the coefficients
+        c = synth.config1()
+        src = dfr.to_c(dfr.fit_inverse_sip(c["src"][0], 4)[0])
+        tgt = dfr.to_c(c["tgt"])
+        img = torch.from_numpy(c["images"][0]).cuda()
+        coef = torch.empty_like(img)
+        bb = (0, 0, 4096, 4096)
+        o = torch.empty((4096, 4096), device="cuda")
+        f = torch.empty_like(o)
+        pre = lambda: dfr.bspline_prefilter(img, out=coef)
+        fwd = lambda: dfr.reproject(coef, src, tgt, bbox=bb, order="bspline3", out=o, fp_out=f,
+                                    prefiltered=True)
+        pre(); fwd()
+        t_p = _events_time(pre, args.steps, flush)[0]
+        t_f = _events_time(fwd, args.steps, flush)[0]
+        out.append({"workload": "4096^2 SIP3 -> 4096^2 TAN, cubic B-spline, split",
+                    "prefilter_ms": t_p, "forward_ms": t_f,
+                    "forward_mpix_s": 16.777216 / t_f * 1e3,
+                    "roofline_frac_hbm": (12 * 16777216 / (t_f * 1e-3)) / 1e9 / _peaks()[0]})
     if args.workload in ("coadd32", "all"):
         # the stack configuration co-added onto its 12000x8000 target, then normalised
         c = synth.config4()
@@ -500,7 +520,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sip3_4096",
                     choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "coadd32",
-                             "tsip4096", "lanczos4096", "all"],
+                             "tsip4096", "lanczos4096", "bspline4096", "all"],
                     help="sip3_4096: the bench line; the others print secondary measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

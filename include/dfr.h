@@ -55,6 +55,8 @@ extern "C" {
 #define DFR_BILINEAR 1
 #define DFR_BICUBIC  2   /* Keys cubic convolution, a = -0.5 */
 #define DFR_LANCZOS3 3   /* Lanczos-3 (6x6 taps, weights normalised per axis); forward only */
+#define DFR_BSPLINE3 4   /* cubic B-spline on prefiltered coefficients (dfr_bspline_prefilter), */
+                         /* mirror boundary, footprint 1 where covered; forward only           */
 
 /* flags */
 #define DFR_FP64           0u  /* all-FP64 per pixel: the printed formulas, with libm trig   */
@@ -123,7 +125,8 @@ int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]);
 /* Reproject one source image onto a bounding box of the target grid (Sec. 3.1 steps 1-3,
  * Sec. 3.2). src_img: device, src->naxis[1] rows, row stride src_pitch. out: device,
  * out_h rows of out_w values, row stride out_pitch. footprint: device, same layout, nullable.
- * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC / DFR_LANCZOS3. flags: DFR_FP64 or DFR_SPLIT, optionally
+ * order: DFR_NEAREST / DFR_BILINEAR / DFR_BICUBIC / DFR_LANCZOS3 / DFR_BSPLINE3 (src_img then
+ * holds B-spline coefficients). flags: DFR_FP64 or DFR_SPLIT, optionally
  * | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK. Without DFR_NAN_MASK, NaN source pixels
  * propagate into the values they touch. coords_out (nullable, device): 2*out_w*out_h doubles,
  * the source position (x then y per pixel, row-major) exactly as the kernel used it, NaN where
@@ -161,6 +164,16 @@ int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
  * dfr_reproject_batch. */
 int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                                 int32_t order, uint32_t flags, void* stream);
+
+/* Cubic B-spline prefilter (the interpolation coefficients of DFR_BSPLINE3): per row, then per
+ * column, the recursive filter with pole z = sqrt(3) - 2 and gain 6 (Unser, Aldroubi & Eden,
+ * 1991; the causal start summed over a mirrored horizon, the anticausal start in closed form),
+ * with mirror (whole-sample symmetric) boundaries, so that the cubic B-spline through the
+ * coefficients passes through every source pixel. img / coef: device, h rows of w values, row
+ * strides pitch / coef_pitch; coef may equal img (in place, same stride). A reprojection with
+ * DFR_BSPLINE3 takes coef as its source image. Asynchronous on `stream`. */
+int dfr_bspline_prefilter(const float* img, int64_t pitch, int32_t w, int32_t h, float* coef,
+                          int64_t coef_pitch, void* stream);
 
 /* Co-add (stack) n exposures onto one target grid: for every target pixel p covered by a
  * frame, sum_vf[p] += value_f(p) * footprint_f(p) and sum_f[p] += footprint_f(p), with value

@@ -18,6 +18,11 @@ Readings taken here:
   * lanczos3 (an extension beyond the paper's three schemes): the Lanczos kernel
     L(d) = sinc(d) sinc(d / 3) for |d| < 3, taps floor(x) - 2 .. floor(x) + 3, weights divided
     by their sum along each axis (so they sum to 1 and a constant is reproduced).
+  * bspline3 (an extension beyond the paper's three schemes): the cubic B-spline through the
+    image. The source is first turned into B-spline coefficients by the recursive prefilter
+    (``bspline3_prefilter``); evaluation uses the B-spline weights on taps floor(x) - 1 ..
+    floor(x) + 2, with the coefficients continued by mirroring (whole-sample symmetric) outside
+    the image, so a covered pixel has footprint 1.
   * FP64 snapping: a coordinate within 1e-9 px of an integer is taken as that integer (so that
     an identity map returns its input bit for bit despite round-off in the transform).
 """
@@ -25,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NEAREST, BILINEAR, BICUBIC, LANCZOS3 = 0, 1, 2, 3
+NEAREST, BILINEAR, BICUBIC, LANCZOS3, BSPLINE3 = 0, 1, 2, 3, 4
 SNAP_PX = 1e-9
 
 
@@ -46,6 +51,51 @@ def lanczos3_kernel(d):
     return np.where(np.abs(d) < 3.0, np.sinc(d) * np.sinc(d / 3.0), 0.0)
 
 
+def bspline3_kernel(d):
+    """Cubic B-spline: 2/3 - |d|^2 + |d|^3 / 2 for |d| <= 1, (2 - |d|)^3 / 6 for 1 < |d| < 2."""
+    d = np.abs(np.asarray(d, dtype=np.float64))
+    return np.where(d <= 1.0, 2.0 / 3.0 - d * d + 0.5 * d ** 3,
+                    np.where(d < 2.0, (2.0 - d) ** 3 / 6.0, 0.0))
+
+
+def mirror_index(i, n):
+    """Whole-sample symmetric extension of integer indices over [0, n)."""
+    i = np.asarray(i)
+    if n == 1:
+        return np.zeros_like(i)
+    p = 2 * (n - 1)
+    i = np.mod(i, p)
+    return np.where(i < n, i, p - i)
+
+
+def bspline3_prefilter_1d(s, axis):
+    """Cubic B-spline coefficients along one axis (mirror boundaries): the recursive filter of
+    Unser, Aldroubi & Eden (1991) with pole z = sqrt(3) - 2 and gain 6 = (1 - z)(1 - 1/z):
+    causal c+[k] = 6 s[k] + z c+[k-1] from c+[0] = sum_j z^j 6 s[mirror(j)], anticausal
+    c[k] = z (c[k+1] - c+[k]) from c[n-1] = z / (z^2 - 1) (c+[n-1] + z c+[n-2])."""
+    s = np.moveaxis(np.asarray(s, dtype=np.float64), axis, 0)
+    n = s.shape[0]
+    if n == 1:
+        return np.moveaxis(s.copy(), 0, axis)
+    z = np.sqrt(3.0) - 2.0
+    horizon = int(np.ceil(np.log(1e-17) / np.log(abs(z))))
+    j = np.arange(horizon)
+    cp = np.empty_like(s)
+    cp[0] = np.tensordot(z ** j, 6.0 * s[mirror_index(j, n)], axes=(0, 0))
+    for k in range(1, n):
+        cp[k] = 6.0 * s[k] + z * cp[k - 1]
+    c = np.empty_like(s)
+    c[n - 1] = z / (z * z - 1.0) * (cp[n - 1] + z * cp[n - 2])
+    for k in range(n - 2, -1, -1):
+        c[k] = z * (c[k + 1] - cp[k])
+    return np.moveaxis(c, 0, axis)
+
+
+def bspline3_prefilter(img):
+    """2-D cubic B-spline coefficients of an image: rows, then columns."""
+    return bspline3_prefilter_1d(bspline3_prefilter_1d(img, 1), 0)
+
+
 def taps_1d(coord, order, a=-0.5):
     """(first tap index, weights[k, n]) along one axis for the given scheme."""
     if order == NEAREST:
@@ -62,6 +112,9 @@ def taps_1d(coord, order, a=-0.5):
     if order == LANCZOS3:
         w = np.stack([lanczos3_kernel(t + 2.0 - k) for k in range(6)])
         return (i0 - 2).astype(np.int64), w / w.sum(axis=0)
+    if order == BSPLINE3:
+        w = np.stack([bspline3_kernel(t + 1.0 - k) for k in range(4)])
+        return (i0 - 1).astype(np.int64), w
     raise ValueError("order")
 
 
@@ -96,6 +149,15 @@ def interpolate(img, x, y, order, valid=None, a=-0.5, use_snap=True, nan_mask=Fa
     ys = np.where(ok, y, 0.0)
     ix, wx = taps_1d(xs, order, a)
     iy, wy = taps_1d(ys, order, a)
+    if order == BSPLINE3:
+        # img holds B-spline coefficients (bspline3_prefilter); mirrored outside the image
+        val = np.zeros(x.shape)
+        for j in range(4):
+            yy = mirror_index(iy + j, H)
+            for i in range(4):
+                xx = mirror_index(ix + i, W)
+                val += wx[i] * wy[j] * img[yy, xx].astype(np.float64)
+        return np.where(ok, val, 0.0), np.where(ok, 1.0, 0.0)
     num = np.zeros(x.shape)
     fp = np.zeros(x.shape)
     for j in range(wy.shape[0]):

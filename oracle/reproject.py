@@ -15,7 +15,7 @@ from . import interp as _interp
 from . import wcs as _wcs
 
 ORDERS = {"nearest": _interp.NEAREST, "bilinear": _interp.BILINEAR, "bicubic": _interp.BICUBIC,
-          "lanczos3": _interp.LANCZOS3}
+          "lanczos3": _interp.LANCZOS3, "bspline3": _interp.BSPLINE3}
 CHUNK = 1 << 20
 
 

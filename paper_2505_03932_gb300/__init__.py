@@ -20,13 +20,15 @@ __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
     "coadd", "coadd_normalize", "calculate_reprojection",
-    "Reproject", "device_status", "NEAREST", "BILINEAR", "BICUBIC", "LANCZOS3", "FP64", "SPLIT",
+    "Reproject", "device_status", "bspline_prefilter", "NEAREST", "BILINEAR", "BICUBIC",
+    "LANCZOS3", "BSPLINE3", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA", "NAN_MASK",
 ]
 
-NEAREST, BILINEAR, BICUBIC, LANCZOS3 = 0, 1, 2, 3
+NEAREST, BILINEAR, BICUBIC, LANCZOS3, BSPLINE3 = 0, 1, 2, 3, 4
 FP64, SPLIT, EXACT_INVERSE, NO_TMA, NAN_MASK = 0, 1, 2, 4, 8
-ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC, "lanczos3": LANCZOS3}
+ORDERS = {"nearest": NEAREST, "bilinear": BILINEAR, "bicubic": BICUBIC, "lanczos3": LANCZOS3,
+          "bspline3": BSPLINE3}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.environ.get("DFR_LIBRARY") or os.path.join(_HERE, "libdfr.so")
 
@@ -97,6 +99,9 @@ def lib():
         L.dfr_coadd_normalize.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.dfr_bspline_prefilter.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
         L.dfr_device_status.argtypes = [ctypes.c_void_p]
         _LIB = L
@@ -217,16 +222,40 @@ def _order(order):
     return ORDERS[order] if isinstance(order, str) else int(order)
 
 
+def bspline_prefilter(img, out=None, stream=None):
+    """Cubic B-spline coefficients of a device image (dfr_bspline_prefilter); ``out`` may be
+    ``img`` itself (in place)."""
+    torch = _torch()
+    img = _dev_f32(img, "img")
+    if out is None:
+        out = torch.empty_like(img)
+    out = _dev_f32(out, "out")
+    h, w = img.shape
+    _check(lib().dfr_bspline_prefilter(ctypes.c_void_p(img.data_ptr()), img.stride(0), w, h,
+                                       ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                       _stream_ptr(stream)))
+    return out
+
+
+def _source_for(img, order, prefiltered, stream=None):
+    """The image a launch reads: for the B-spline order its coefficients (prefiltered here
+    unless the caller passes them)."""
+    if _order(order) == BSPLINE3 and not prefiltered:
+        return bspline_prefilter(img, stream=stream)
+    return img
+
+
 def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilinear",
               precision="split", exact_inverse=False, footprint=True, coords=False, tma=True,
-              out=None, fp_out=None, stream=None, nan_mask=False):
+              out=None, fp_out=None, stream=None, nan_mask=False, prefiltered=False):
     """Reproject a device image onto the target grid (dfr_reproject).
 
     shape_out (h, w) defaults to the target NAXIS; bbox = (x0, y0, w, h) selects part of the
-    target grid; nan_mask: NaN source pixels are missing (no weight). Returns (value, footprint
-    or None[, coords (h, w, 2) float64])."""
+    target grid; nan_mask: NaN source pixels are missing (no weight); order "bspline3"
+    prefilters the image first unless ``prefiltered`` (then src_img holds the coefficients).
+    Returns (value, footprint or None[, coords (h, w, 2) float64])."""
     torch = _torch()
-    src_img = _dev_f32(src_img, "src_img")
+    src_img = _source_for(_dev_f32(src_img, "src_img"), order, prefiltered, stream)
     if bbox is None:
         if shape_out is None:
             nax = tgt_wcs.naxis if isinstance(tgt_wcs, DfrWcs) else tgt_wcs["naxis"]
@@ -253,16 +282,17 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
 
 def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear",
                     precision="split", outs=None, fps=None, footprint=True, stream=None,
-                    nan_mask=False):
+                    nan_mask=False, prefiltered=False):
     """Reproject many exposures in one persistent launch (dfr_reproject_batch).
 
     bboxes default to dfr_target_bbox per frame. Returns (values, footprints) lists."""
     torch = _torch()
     n = len(images)
     frames = (DfrFrame * max(n, 1))()
-    vals, fpl = [], []
+    vals, fpl, keep = [], [], []
     for i in range(n):
-        img = _dev_f32(images[i], "images[%d]" % i)
+        img = _source_for(_dev_f32(images[i], "images[%d]" % i), order, prefiltered, stream)
+        keep.append(img)
         bb = bboxes[i] if bboxes is not None else target_bbox(src_wcs_list[i], tgt_wcs)
         x0, y0, w, h = (int(v) for v in bb)
         o = outs[i] if outs is not None else torch.empty((max(h, 1), max(w, 1)),
@@ -313,7 +343,7 @@ def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=Non
 
 
 def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precision="split",
-          sum_vf=None, sum_f=None, stream=None, tma=True, nan_mask=False):
+          sum_vf=None, sum_f=None, stream=None, tma=True, nan_mask=False, prefiltered=False):
     """Co-add exposures onto the target grid (dfr_coadd): sum_vf += value * footprint and
     sum_f += footprint per target pixel, frames in order. ``sum_vf`` / ``sum_f`` (device,
     target-sized) are created zeroed when not given. ``bboxes`` default to (0, 0, 0, 0), which
@@ -336,7 +366,7 @@ def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precisio
     frames = (DfrFrame * max(n, 1))()
     keep = []
     for i in range(n):
-        img = _dev_f32(images[i], "images[%d]" % i)
+        img = _source_for(_dev_f32(images[i], "images[%d]" % i), order, prefiltered, stream)
         keep.append(img)
         fr = frames[i]
         fr.wcs = to_c(src_wcs_list[i])

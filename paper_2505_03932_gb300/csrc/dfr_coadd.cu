@@ -28,7 +28,8 @@ const void* coadd_kernel(const FwdPlan& p0) {
     case DFR_NEAREST: return coadd_for_order<DFR_NEAREST>(split, p0.isip_deg);
     case DFR_BILINEAR: return coadd_for_order<DFR_BILINEAR>(split, p0.isip_deg);
     case DFR_BICUBIC: return coadd_for_order<DFR_BICUBIC>(split, p0.isip_deg);
-    default: return coadd_for_order<DFR_LANCZOS3>(split, p0.isip_deg);
+    case DFR_LANCZOS3: return coadd_for_order<DFR_LANCZOS3>(split, p0.isip_deg);
+    default: return coadd_for_order<DFR_BSPLINE3>(split, p0.isip_deg);
   }
 }
 

@@ -155,6 +155,29 @@ template <> struct Taps<DFR_NEAREST> { static constexpr int n = 1, lo = 0; };
 template <> struct Taps<DFR_BILINEAR> { static constexpr int n = 2, lo = 0; };
 template <> struct Taps<DFR_BICUBIC> { static constexpr int n = 4, lo = -1; };
 template <> struct Taps<DFR_LANCZOS3> { static constexpr int n = 6, lo = -2; };
+template <> struct Taps<DFR_BSPLINE3> { static constexpr int n = 4, lo = -1; };
+
+// Whole-sample symmetric (mirror) extension of index i over [0, n): ... 2 1 | 0 1 2 ... n-1 |
+// n-2 ... (period 2 (n - 1)). Used for the B-spline taps outside the image.
+__device__ __forceinline__ int mirror_index(int i, int n) {
+  if (n <= 1) return 0;
+  const int p = 2 * (n - 1);
+  i %= p;
+  if (i < 0) i += p;
+  return i < n ? i : p - i;
+}
+
+// Cubic B-spline weights at distances 1 + t, t, 1 - t, 2 - t: (1-t)^3/6, 2/3 - t^2 + t^3/2,
+// 2/3 - (1-t)^2 + (1-t)^3/2, t^3/6.
+template <typename T>
+__device__ __forceinline__ void bspline3_weights(T t, T* w) {
+  const T s = T(1) - t;
+  const T sixth = T(1) / T(6), two3 = T(2) / T(3);
+  w[0] = (s * s) * (s * sixth);
+  w[1] = fma(t * t, fma(T(0.5), t, T(-1)), two3);
+  w[2] = fma(s * s, fma(T(0.5), s, T(-1)), two3);
+  w[3] = (t * t) * (t * sixth);
+}
 
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
@@ -199,6 +222,8 @@ __device__ __forceinline__ void weights(T t, T* w) {
     w[1] = t;
   } else if (ORDER == DFR_LANCZOS3) {
     lanczos3_weights<T>(t, w);
+  } else if (ORDER == DFR_BSPLINE3) {
+    bspline3_weights<T>(t, w);
   } else {
     // Keys cubic convolution, a = -0.5, at distances 1+t, t, 1-t, 2-t
     const T s = T(1) - t;
@@ -227,6 +252,12 @@ __device__ __forceinline__ void weights2(float2 t, float2* w) {
     lanczos3_weights<float>(t.y, wy);
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] = make_float2(wx[k], wy[k]);
+  } else if (ORDER == DFR_BSPLINE3) {
+    float wx[4], wy[4];
+    bspline3_weights<float>(t.x, wx);
+    bspline3_weights<float>(t.y, wy);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = make_float2(wx[k], wy[k]);
   } else {
     const float2 s = __fadd2_rn(one, nt);
     const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);

@@ -77,7 +77,8 @@ static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
     case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, batch, p0.isip_deg);
     case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, batch, p0.isip_deg);
     case DFR_BICUBIC: return kernel_for_order<DFR_BICUBIC>(split, batch, p0.isip_deg);
-    default: return kernel_for_order<DFR_LANCZOS3>(split, batch, p0.isip_deg);
+    case DFR_LANCZOS3: return kernel_for_order<DFR_LANCZOS3>(split, batch, p0.isip_deg);
+    default: return kernel_for_order<DFR_BSPLINE3>(split, batch, p0.isip_deg);
   }
 }
 

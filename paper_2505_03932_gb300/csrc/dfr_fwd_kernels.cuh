@@ -64,6 +64,26 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
       weights<ORDER, double>(tx, wx);
       weights<ORDER, double>(ty, wy);
       const int ix = int(fx) + T::lo, iy = int(fy) + T::lo;
+      if (ORDER == DFR_BSPLINE3) {
+        // coefficients continue by mirroring outside the image; footprint 1
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < T::n; ++b) {
+          const int yy = mirror_index(iy + b, P.H);
+          double row = 0.0;
+#pragma unroll
+          for (int a = 0; a < T::n; ++a)
+            row += wx[a] * double(__ldg(P.img + int64_t(yy) * P.pitch + mirror_index(ix + a, P.W)));
+          acc += wy[b] * row;
+        }
+        if (ACC) {
+          put_pixel<true>(P.out + o, P.fp + o, float(acc), 1.f);
+        } else {
+          P.out[o] = float(acc);
+          if (P.fp) P.fp[o] = 1.f;
+        }
+        continue;
+      }
       double num = 0.0, sx = 0.0, sy = 0.0;
 #pragma unroll
       for (int a = 0; a < T::n; ++a) {
@@ -154,6 +174,22 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
   if (ORDER == DFR_NEAREST) {
     const float v = S(ix, iy, 0, 0);
     return interior ? make_float2(v, 1.f) : make_float2(0.f, 0.f);
+  }
+  if (ORDER == DFR_BSPLINE3 && !interior) {
+    // B-spline coefficients continue by mirroring outside the image; footprint 1
+    float num = 0.f;
+#pragma unroll
+    for (int k = 0; k < T::n; ++k) {
+      const int yy = mirror_index(iy + k, H);
+      float row = 0.f;
+#pragma unroll
+      for (int q = 0; q < T::n; ++q) {
+        const int xx = mirror_index(ix + q, W);
+        row = fmaf(w[q].x, S(xx - q, yy - k, k, q), row);
+      }
+      num = fmaf(w[k].y, row, num);
+    }
+    return make_float2(num, 1.f);
   }
   float sx = 0.f, sy = 0.f;
   if (!interior) {
@@ -374,7 +410,12 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
       }
       // first tap relative to the box origin
       const int cx = ix + a.bx + T::lo - tb.bx0, cy = iy + a.by + T::lo - tb.by0;
-      const bool in_box = tb.use_box && cx >= 0 && cx + T::n <= bw && cy >= 0 && cy + T::n <= bh;
+      bool in_box = tb.use_box && cx >= 0 && cx + T::n <= bw && cy >= 0 && cy + T::n <= bh;
+      if (ORDER == DFR_BSPLINE3) {
+        // mirrored taps (pixels near the image edge) may leave the box: global memory then
+        const int ixa = ix + a.bx + T::lo, iya = iy + a.by + T::lo;
+        in_box = in_box && ixa >= 0 && ixa + T::n <= Q.W && iya >= 0 && iya + T::n <= Q.H;
+      }
       if (in_box) {
         const int bx0 = tb.bx0, by0 = tb.by0;
         auto SB = [=](int ixa, int iya, int k, int q) -> float {

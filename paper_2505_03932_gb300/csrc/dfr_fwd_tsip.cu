@@ -21,7 +21,8 @@ const void* tsip_kernel(const FwdPlan& p0) {
     case DFR_NEAREST: return tsip_for_order<DFR_NEAREST>(p0.isip_deg);
     case DFR_BILINEAR: return tsip_for_order<DFR_BILINEAR>(p0.isip_deg);
     case DFR_BICUBIC: return tsip_for_order<DFR_BICUBIC>(p0.isip_deg);
-    default: return tsip_for_order<DFR_LANCZOS3>(p0.isip_deg);
+    case DFR_LANCZOS3: return tsip_for_order<DFR_LANCZOS3>(p0.isip_deg);
+    default: return tsip_for_order<DFR_BSPLINE3>(p0.isip_deg);
   }
 }
 

@@ -320,7 +320,8 @@ void size_box(FwdPlan& P) {
   const double A = kTileW - 1, B = kTileH - 1;
   const double dev = (kxx * A * A + 2 * kxy * A * B + kyy * B * B) / 8.0;
   P.box_margin = 1 + int(std::ceil(4.0 * dev));
-  const int ext = (P.order == DFR_LANCZOS3) ? 6 : (P.order == DFR_BICUBIC) ? 4 : 2;
+  const int ext = (P.order == DFR_LANCZOS3) ? 6
+                  : (P.order == DFR_BICUBIC || P.order == DFR_BSPLINE3) ? 4 : 2;
   const double sx = 1.1 * (jxx * (kTileW - 1) + jxy * (kTileH - 1)) + 1.0;
   const double sy = 1.1 * (jyx * (kTileW - 1) + jyy * (kTileH - 1)) + 1.0;
   int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
@@ -339,9 +340,11 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   int rc;
   if ((rc = check_wcs(src, "source")) != DFR_OK) return rc;
   if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
-  if (order < DFR_NEAREST || order > DFR_LANCZOS3)
-    return fail(DFR_ERR_INVALID_ARG,
-                "order must be DFR_NEAREST, DFR_BILINEAR, DFR_BICUBIC or DFR_LANCZOS3");
+  if (order < DFR_NEAREST || order > DFR_BSPLINE3)
+    return fail(DFR_ERR_INVALID_ARG, "order must be DFR_NEAREST, DFR_BILINEAR, DFR_BICUBIC, "
+                                     "DFR_LANCZOS3 or DFR_BSPLINE3");
+  if (order == DFR_BSPLINE3 && (flags & DFR_NAN_MASK))
+    return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK does not apply to B-spline coefficients");
   if (flags & ~(DFR_SPLIT | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK))
     return fail(DFR_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags);
   if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative output size");
@@ -1371,6 +1374,20 @@ extern "C" int dfr_coadd_normalize(const float* sum_vf, const float* sum_f, int6
   return DFR_OK;
 }
 
+extern "C" int dfr_bspline_prefilter(const float* img, int64_t pitch, int32_t w, int32_t h,
+                                     float* coef, int64_t coef_pitch, void* stream) {
+  if (w < 0 || h < 0) return fail(DFR_ERR_INVALID_ARG, "negative size");
+  if (w == 0 || h == 0) return DFR_OK;
+  if (!img || !coef) return fail(DFR_ERR_INVALID_ARG, "NULL buffer");
+  if (pitch < w || coef_pitch < w) return fail(DFR_ERR_INVALID_ARG, "pitch < width");
+  if (img == coef && pitch != coef_pitch)
+    return fail(DFR_ERR_INVALID_ARG, "in-place prefilter needs equal strides");
+  cudaError_t e = launch_bspline_prefilter(img, pitch, w, h, coef, coef_pitch,
+                                           static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dfr_bspline_prefilter launch");
+  return DFR_OK;
+}
+
 namespace dfr {
 namespace {
 
@@ -1394,8 +1411,9 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       double* grad_params, void* stream) {
   if (flags & DFR_NAN_MASK)
     return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK is not supported by the adjoint");
-  if (order == DFR_LANCZOS3)
-    return fail(DFR_ERR_INVALID_ARG, "DFR_LANCZOS3 is not supported by the adjoint");
+  if (order == DFR_LANCZOS3 || order == DFR_BSPLINE3)
+    return fail(DFR_ERR_INVALID_ARG, "%s is not supported by the adjoint",
+                order == DFR_LANCZOS3 ? "DFR_LANCZOS3" : "DFR_BSPLINE3");
   FwdPlan P;
   // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
   // split path stages source and gradient boxes by tile, as sized by the plan

@@ -137,6 +137,8 @@ int backward_threads_for(const FwdPlan& p0, int fd);
 const void* backward_tile_kernel(int order, int ideg, int fd);  // dfr_bwd_tile.cu
 const void* coadd_kernel(const FwdPlan& p0);                      // dfr_coadd.cu
 const void* tsip_kernel(const FwdPlan& p0);                       // dfr_fwd_tsip.cu
+cudaError_t launch_bspline_prefilter(const float* img, int64_t pitch, int32_t w, int32_t h,
+                                     float* coef, int64_t coef_pitch, cudaStream_t s);
 cudaError_t launch_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch,
                                    int32_t w, int32_t h, float min_weight, float* mean,
                                    int64_t mean_pitch, cudaStream_t s);

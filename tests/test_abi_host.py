@@ -131,7 +131,8 @@ def test_argument_errors_before_any_launch(dfr):
         ctypes.byref(kw.get("s", s)), ctypes.byref(t), kw.get("img", dummy), kw.get("pitch", 64),
         kw.get("out", dummy), None, kw.get("opitch", 64), 0, 0, kw.get("w", 64), kw.get("h", 64),
         kw.get("order", 1), kw.get("flags", 1), None, None)
-    assert call(order=4) == -1
+    assert call(order=5) == -1
+    assert call(order=4, flags=1 | 8) == -1  # B-spline coefficients with the NaN mask
     assert call(flags=64) == -1
     assert call(pitch=10) == -1
     assert call(opitch=10) == -1
@@ -245,3 +246,14 @@ def test_adjoint_refuses_lanczos3(dfr):
                                   ctypes.c_void_p(16), 64, 0, 0, 64, 64, dfr.LANCZOS3, dfr.SPLIT,
                                   None, 0, None, None)
     assert rc == -1 and "LANCZOS3" in L.dfr_last_error().decode()
+
+
+def test_bspline_prefilter_argument_errors(dfr):
+    L = dfr.lib()
+    d = ctypes.c_void_p(16)
+    e = ctypes.c_void_p(32)
+    assert L.dfr_bspline_prefilter(d, 64, 0, 10, d, 64, None) == 0
+    assert L.dfr_bspline_prefilter(d, 64, -1, 10, d, 64, None) == -1
+    assert L.dfr_bspline_prefilter(None, 64, 8, 10, d, 64, None) == -1
+    assert L.dfr_bspline_prefilter(d, 4, 8, 10, e, 64, None) == -1
+    assert L.dfr_bspline_prefilter(d, 64, 8, 10, d, 72, None) == -1  # in place, other stride

@@ -32,7 +32,7 @@ def _frames(n=5, seed=21):
     return srcs, imgs, tgt
 
 
-@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic", "lanczos3"])
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic", "lanczos3", "bspline3"])
 @pytest.mark.parametrize("precision", ["split", "fp64"])
 def test_batch_equals_single_bitwise(order, precision):
     srcs, imgs, tgt = _frames()

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import interp as OI
 from oracle import reproject as OR
 from oracle import wcs as OW
 
@@ -142,7 +143,7 @@ def test_tma_and_direct_gather_agree_bitwise(case):
     else:
         src, tgt, img = _far_pair(case.endswith("target_sip"))
     bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
-    for order in ("nearest", "bilinear", "bicubic", "lanczos3"):
+    for order in ("nearest", "bilinear", "bicubic", "lanczos3", "bspline3"):
         a = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=True)
         b = gpu(src, tgt, to_dev(img), order, "split", bbox, tma=False)
         for u, v in zip(a, b):
@@ -300,3 +301,38 @@ def test_lanczos3_identity_and_constant():
         v, f = v.cpu().numpy(), f.cpu().numpy()
         assert (f > 0).mean() > 0.5
         assert np.abs(v[f > 0] - 2.5).max() < 1e-5
+
+
+
+@pytest.mark.parametrize("shape", [(300, 200), (37, 53), (1, 17), (17, 1), (2, 9)])
+def test_bspline_prefilter_matches_oracle(shape):
+    """GPU prefilter (FP32 recursion, rows then columns) against the oracle's FP64 coefficients,
+    element by element (1e-5 of the largest coefficient), out of place and in place."""
+    h, w = shape
+    img = synth.rng_for(40).standard_normal((h, w)).astype(np.float32) * 10
+    ref = OI.bspline3_prefilter(img.astype(np.float64))
+    d = to_dev(img)
+    c = dfr().bspline_prefilter(d).cpu().numpy()
+    tol = 1e-5 * np.abs(ref).max()
+    assert np.abs(c - ref).max() <= tol
+    dfr().bspline_prefilter(d, out=d)
+    assert np.array_equal(d.cpu().numpy(), c)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_bspline3_reprojection(precision):
+    """B-spline reprojection against the oracle's evaluation on its own FP64 coefficients at the
+    GPU's coordinates (values 1e-5; footprint 1 exactly where covered); the identity map returns
+    the image to FP32 rounding of the coefficients."""
+    src, tgt, img = _small_sip(w=400, h=300, seed=41)
+    bbox = (0, 0, tgt["naxis"][0], tgt["naxis"][1])
+    val, fp, cr = gpu(src, tgt, to_dev(img), "bspline3", precision, bbox)
+    coef = OI.bspline3_prefilter(img.astype(np.float64))
+    e, fe = value_check(coef, "bspline3", val, fp, cr, precision)
+    assert e <= VALUE_RTOL and fe == 0.0
+    assert set(np.unique(fp)) <= {0.0, 1.0} and (fp == 1).mean() > 0.5
+    plain = synth.tan_wcs(300, 200)
+    im2 = synth.sky_image(300, 200, 20, synth.rng_for(42))
+    v, f = dfr().reproject(to_dev(im2), plain, plain, order="bspline3", precision=precision)
+    assert np.abs(v.cpu().numpy() - im2).max() <= 1e-5 * max(np.abs(im2).max(), 1.0)
+    assert bool((f == 1).all())
