@@ -137,6 +137,22 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
                   int32_t x0, int32_t y0, int32_t out_w, int32_t out_h,
                   int32_t order, uint32_t flags, double* coords_out, void* stream);
 
+/* dfr_reproject from HOST memory to HOST memory, with the copies overlapped with the work:
+ * the bounding box is cut into bands of 32-pixel cell rows; each band's source rows go
+ * host->device on one library stream (only rows no earlier band copied), its kernel runs on a
+ * second stream once they are in, and its value / footprint rows go device->host on a third,
+ * so both copy directions and the compute overlap. host_img: src->naxis[1] rows, stride
+ * host_pitch; host_out / host_fp (nullable): out_h rows of out_w, stride out_pitch. The
+ * library holds the device copies of source and outputs (cached per device, grown on demand).
+ * Page-locked host buffers (cudaHostAlloc / cudaHostRegister) let the copies run
+ * asynchronously; pageable memory works but serialises them. Returns once the outputs are in
+ * host memory. The FP64 path, DFR_BSPLINE3 (prefilter first) and boxes of one band run as one
+ * band. Same arithmetic, so the same bits, as dfr_reproject. */
+int dfr_reproject_host(const dfr_wcs* src, const dfr_wcs* tgt, const float* host_img,
+                       int64_t host_pitch, float* host_out, float* host_fp, int64_t out_pitch,
+                       int32_t x0, int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
+                       uint32_t flags);
+
 /* Reproject n exposures onto one target grid in one CUDA-graph launch (the paper's pipeline
  * stacks >1000 exposures, Sec. 2). Every frame's pixels are computed with exactly the
  * arithmetic of dfr_reproject for the same bounding box and flags, so results are equal bit

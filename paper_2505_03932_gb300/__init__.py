@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
-    "coadd", "coadd_normalize", "calculate_reprojection",
+    "coadd", "coadd_normalize", "reproject_host", "calculate_reprojection",
     "Reproject", "device_status", "bspline_prefilter", "NEAREST", "BILINEAR", "BICUBIC",
     "LANCZOS3", "BSPLINE3", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA", "NAN_MASK",
@@ -102,6 +102,10 @@ def lib():
         L.dfr_bspline_prefilter.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_void_p]
+        L.dfr_reproject_host.argtypes = [
+            ctypes.POINTER(DfrWcs), ctypes.POINTER(DfrWcs), ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
         L.dfr_device_status.argtypes = [ctypes.c_void_p]
         _LIB = L
@@ -427,23 +431,72 @@ def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinea
     return gs, gp
 
 
+def _host_ptr(a, name, shape=None):
+    """(pointer, row stride in elements) of a host float32 2-D array or CPU tensor."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or a.dim() != 2 or a.stride(1) != 1:
+            raise ValueError("%s must be a 2-D float32 host tensor with unit x stride" % name)
+        t = a
+        ptr, stride = t.data_ptr(), t.stride(0)
+    else:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.ndim == 2
+                and a.strides[1] == 4 and a.strides[0] % 4 == 0):
+            raise ValueError("%s must be a 2-D float32 array with unit x stride" % name)
+        t = a
+        ptr, stride = a.ctypes.data, a.strides[0] // 4
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ptr, stride
+
+
+def reproject_host(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilinear",
+                   precision="split", exact_inverse=False, out=None, fp_out=None,
+                   footprint=True, nan_mask=False):
+    """Host image in, host (value, footprint) out (dfr_reproject_host): bands of the output are
+    copied in, computed and copied out on overlapping streams. Inputs and outputs are float32
+    numpy arrays or CPU tensors; page-locked tensors (``pin_memory()``) let the copies overlap.
+    Returns (value, footprint or None), the given ``out`` / ``fp_out`` when passed."""
+    if bbox is None:
+        if shape_out is None:
+            nax = tgt_wcs.naxis if isinstance(tgt_wcs, DfrWcs) else tgt_wcs["naxis"]
+            shape_out = (int(nax[1]), int(nax[0]))
+        bbox = (0, 0, int(shape_out[1]), int(shape_out[0]))
+    x0, y0, w, h = (int(v) for v in bbox)
+    if not isinstance(src_img, np.ndarray) and not hasattr(src_img, "data_ptr"):
+        src_img = np.ascontiguousarray(src_img, dtype=np.float32)
+    ip, istride = _host_ptr(src_img, "src_img")
+    if out is None:
+        out = np.empty((h, w), np.float32)
+    op, ostride = _host_ptr(out, "out", (h, w))
+    fp = None
+    fpp = 0
+    if footprint:
+        fp = fp_out if fp_out is not None else np.empty((h, w), np.float32)
+        fpp, fstride = _host_ptr(fp, "fp_out", (h, w))
+        if fstride != ostride:
+            raise ValueError("out and fp_out must share the row stride")
+    _check(lib().dfr_reproject_host(
+        ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)), ctypes.c_void_p(ip), istride,
+        ctypes.c_void_p(op), ctypes.c_void_p(fpp), ostride, x0, y0, w, h, _order(order),
+        _flags(precision, exact_inverse, True, nan_mask)))
+    return out, fp
+
+
 def calculate_reprojection(source_img, source_wcs, target_wcs, shape_out=None, order="bilinear",
                            precision="split"):
     """Paper-style call (Sec. 2): host image in, host (value, footprint) out.
 
-    ``source_wcs`` / ``target_wcs`` may be WCS records or FITS header text. The image is copied
-    to the current CUDA device, reprojected there and copied back; ``shape_out`` defaults to
-    the target NAXIS (the input shape when the target header has none of its own)."""
-    torch = _torch()
+    ``source_wcs`` / ``target_wcs`` may be WCS records or FITS header text; ``shape_out``
+    defaults to the target NAXIS. The work runs on the current CUDA device through
+    dfr_reproject_host (copies overlapped with the computation)."""
     if isinstance(source_wcs, (str, bytes)):
         source_wcs = wcs_from_header(source_wcs)
     if isinstance(target_wcs, (str, bytes)):
         target_wcs = wcs_from_header(target_wcs)
-    host = torch.as_tensor(np.asarray(source_img, dtype=np.float32))
-    dev = host.to("cuda", non_blocking=True)
-    val, fp = reproject(dev, source_wcs, target_wcs, shape_out=shape_out, order=order,
-                        precision=precision)
-    return val.cpu().numpy(), fp.cpu().numpy()
+    img = np.ascontiguousarray(source_img, dtype=np.float32)
+    return reproject_host(img, source_wcs, target_wcs, shape_out=shape_out, order=order,
+                          precision=precision)
 
 
 def _autograd():

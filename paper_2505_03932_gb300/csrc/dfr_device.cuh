@@ -173,10 +173,11 @@ template <typename T>
 __device__ __forceinline__ void bspline3_weights(T t, T* w) {
   const T s = T(1) - t;
   const T sixth = T(1) / T(6), two3 = T(2) / T(3);
-  w[0] = (s * s) * (s * sixth);
-  w[1] = fma(t * t, fma(T(0.5), t, T(-1)), two3);
-  w[2] = fma(s * s, fma(T(0.5), s, T(-1)), two3);
-  w[3] = (t * t) * (t * sixth);
+  const T s2 = s * s, t2 = t * t;
+  w[0] = s2 * (s * sixth);
+  w[1] = fma(t2, fma(T(0.5), t, T(-1)), two3);
+  w[2] = fma(s2, fma(T(0.5), s, T(-1)), two3);
+  w[3] = t2 * (t * sixth);
 }
 
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
@@ -253,11 +254,15 @@ __device__ __forceinline__ void weights2(float2 t, float2* w) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] = make_float2(wx[k], wy[k]);
   } else if (ORDER == DFR_BSPLINE3) {
-    float wx[4], wy[4];
-    bspline3_weights<float>(t.x, wx);
-    bspline3_weights<float>(t.y, wy);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w[k] = make_float2(wx[k], wy[k]);
+    // bspline3_weights for both axes in FP32x2 (each half the same operations, so the same bits)
+    const float2 s = __fadd2_rn(one, nt);
+    const float2 sixth = make_float2(1.f / 6.f, 1.f / 6.f), two3 = make_float2(2.f / 3.f, 2.f / 3.f);
+    const float2 half = make_float2(0.5f, 0.5f), mone = make_float2(-1.f, -1.f);
+    const float2 s2 = __fmul2_rn(s, s), t2 = __fmul2_rn(t, t);
+    w[0] = __fmul2_rn(s2, __fmul2_rn(s, sixth));
+    w[1] = __ffma2_rn(t2, __ffma2_rn(half, t, mone), two3);
+    w[2] = __ffma2_rn(s2, __ffma2_rn(half, s, mone), two3);
+    w[3] = __fmul2_rn(t2, __fmul2_rn(t, sixth));
   } else {
     const float2 s = __fadd2_rn(one, nt);
     const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);

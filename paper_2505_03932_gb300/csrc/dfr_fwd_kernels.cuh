@@ -412,9 +412,19 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
       const int cx = ix + a.bx + T::lo - tb.bx0, cy = iy + a.by + T::lo - tb.by0;
       bool in_box = tb.use_box && cx >= 0 && cx + T::n <= bw && cy >= 0 && cy + T::n <= bh;
       if (ORDER == DFR_BSPLINE3) {
-        // mirrored taps (pixels near the image edge) may leave the box: global memory then
+        // near the image edge the taps are mirrored: the box must hold the mirrored positions
         const int ixa = ix + a.bx + T::lo, iya = iy + a.by + T::lo;
-        in_box = in_box && ixa >= 0 && ixa + T::n <= Q.W && iya >= 0 && iya + T::n <= Q.H;
+        int mx0 = INT_MAX, mx1 = INT_MIN, my0 = INT_MAX, my1 = INT_MIN;
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) {
+          const int mx = mirror_index(ixa + q, Q.W), my = mirror_index(iya + q, Q.H);
+          mx0 = min(mx0, mx);
+          mx1 = max(mx1, mx);
+          my0 = min(my0, my);
+          my1 = max(my1, my);
+        }
+        in_box = tb.use_box && mx0 >= tb.bx0 && mx1 < tb.bx0 + bw && my0 >= tb.by0 &&
+                 my1 < tb.by0 + bh;
       }
       if (in_box) {
         const int bx0 = tb.bx0, by0 = tb.by0;
@@ -499,9 +509,11 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP
   }
   uint32_t phase = 0;  // bit b: parity of the next wait on buffer b
   constexpr bool batch = BATCH;
-  const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;  // cells
+  // cells; a single-frame launch may cover units [unit_begin, unit_begin + grid) only (bands)
+  const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
   const int nunits = (total + kCellsPerCta - 1) / kCellsPerCta;
-  int unit = blockIdx.x;  // grid launch: one unit per CTA; persistent: units from a counter
+  // grid launch: one unit per CTA (from unit_begin); persistent: units from a counter
+  int unit = blockIdx.x + L.unit_begin;
   if (batch) {
     if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
     __syncthreads();

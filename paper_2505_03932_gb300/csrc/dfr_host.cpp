@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <tuple>
 #include <unordered_map>
@@ -1372,6 +1373,198 @@ extern "C" int dfr_coadd_normalize(const float* sum_vf, const float* sum_f, int6
                                          mean_pitch, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_coadd_normalize launch");
   return DFR_OK;
+}
+
+namespace dfr {
+namespace {
+
+// Device copies and streams of the host-to-host entry point, per device.
+struct HostPipe {
+  float* d_src = nullptr;
+  float* d_out = nullptr;
+  float* d_fp = nullptr;
+  size_t src_cap = 0, out_cap = 0;  // floats
+  cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr, d2h_fp = nullptr;
+  std::vector<cudaEvent_t> ev;
+};
+std::map<int, HostPipe> g_pipe;
+
+// One host<->device copy of `rows` rows of `width` floats: a single linear copy when both sides
+// are contiguous, else a pitched copy.
+cudaError_t copy_rows(float* dst, int64_t dpitch, const float* srcp, int64_t spitch,
+                      int64_t width, int64_t rows, cudaMemcpyKind kind, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (dpitch == width && spitch == width)
+    return cudaMemcpyAsync(dst, srcp, size_t(width * rows) * 4, kind, s);
+  return cudaMemcpy2DAsync(dst, size_t(dpitch) * 4, srcp, size_t(spitch) * 4, size_t(width) * 4,
+                           size_t(rows), kind, s);
+}
+
+int grow(float*& p, size_t& cap, size_t need) {
+  if (need <= cap) return DFR_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  DFR_CUDA(cudaMalloc(&p, need * sizeof(float)));
+  cap = need;
+  return DFR_OK;
+}
+
+// Source rows [r0, r1) that the bounding-box rows [t0, t1) read: the FP64 host map on the
+// outline of the band (every 64 px) and its middle row, widened by the interpolation taps, the
+// plan's curvature margin and a safety margin, clipped to the image. All rows when the map is
+// undefined somewhere.
+void band_source_rows(const FwdPlan& P, int t0, int t1, int& r0, int& r1) {
+  HostMap M{&P};
+  double lo = 1e300, hi = -1e300;
+  bool all = false;
+  auto visit = [&](double X, double Y) {
+    double xs, ys;
+    if (!M.eval(X, Y, xs, ys) || !std::isfinite(ys)) {
+      all = true;
+      return;
+    }
+    lo = std::min(lo, ys);
+    hi = std::max(hi, ys);
+  };
+  const int step = 64;
+  for (int y : {t0, (t0 + t1 - 1) / 2, t1 - 1})
+    for (int x = 0;; x = std::min(x + step, P.w - 1)) {
+      visit(P.x0 + x, P.y0 + y);
+      if (x == P.w - 1) break;
+    }
+  for (int x : {0, P.w - 1})
+    for (int y = t0; y < t1; y += step) visit(P.x0 + x, P.y0 + y);
+  if (all || !(lo <= hi)) {
+    r0 = 0;
+    r1 = P.H;
+    return;
+  }
+  // taps (up to 3 rows either side), curvature between samples and inside the outline
+  const int margin = 8 + 2 * P.box_margin;
+  r0 = std::max(0, int(std::floor(lo)) - margin);
+  r1 = std::min(P.H, int(std::ceil(hi)) + margin + 1);
+  if (r1 < r0) r1 = r0;
+}
+
+}  // namespace
+}  // namespace dfr
+
+extern "C" int dfr_reproject_host(const dfr_wcs* src, const dfr_wcs* tgt, const float* host_img,
+                                  int64_t host_pitch, float* host_out, float* host_fp,
+                                  int64_t out_pitch, int32_t x0, int32_t y0, int32_t out_w,
+                                  int32_t out_h, int32_t order, uint32_t flags) {
+  if (!src || !tgt) return fail(DFR_ERR_INVALID_ARG, "NULL WCS");
+  if (out_w < 0 || out_h < 0) return fail(DFR_ERR_INVALID_ARG, "negative output size");
+  if (out_w == 0 || out_h == 0) return DFR_OK;
+  if (!host_img || !host_out) return fail(DFR_ERR_INVALID_ARG, "NULL host buffer");
+  const int W = src->naxis[0], H = src->naxis[1];
+  if (host_pitch < W) return fail(DFR_ERR_INVALID_ARG, "host image pitch < NAXIS1");
+  if (out_pitch < out_w) return fail(DFR_ERR_INVALID_ARG, "output pitch < width");
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  DFR_CUDA(cudaGetDevice(&dev));
+  HostPipe& hp = g_pipe[dev];
+  if (!hp.h2d) {
+    DFR_CUDA(cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking));
+    DFR_CUDA(cudaStreamCreateWithFlags(&hp.comp, cudaStreamNonBlocking));
+    DFR_CUDA(cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking));
+    DFR_CUDA(cudaStreamCreateWithFlags(&hp.d2h_fp, cudaStreamNonBlocking));
+  }
+  // device copies: rows padded to 16 bytes (TMA tensor maps need it)
+  const int64_t dsp = (int64_t(W) + 3) & ~int64_t(3), dop = (int64_t(out_w) + 3) & ~int64_t(3);
+  int rc = grow(hp.d_src, hp.src_cap, size_t(dsp) * size_t(H));
+  if (rc == DFR_OK) rc = grow(hp.d_out, hp.out_cap, size_t(dop) * size_t(out_h) * 2);
+  if (rc != DFR_OK) return rc;
+  hp.d_fp = hp.d_out + dop * out_h;
+  FwdPlan P;
+  rc = cached_plan(src, tgt, hp.d_src, dsp, hp.d_out, hp.d_fp, dop, x0, y0, out_w, out_h, order,
+                   flags, nullptr, -1, P);
+  if (rc != DFR_OK) return rc;
+  const bool banded = (flags & DFR_SPLIT) && order != DFR_BSPLINE3;
+  // bands of R cell rows, R * cells_x a multiple of the cells per unit (bands start on units)
+  int R = P.cells_y, nb = 1;
+  if (banded) {
+    const int q = kCellsPerCta / std::gcd(P.cells_x, kCellsPerCta);
+    R = std::max(1, (P.cells_y + 7) / 8);
+    R = (R + q - 1) / q * q;
+    nb = (P.cells_y + R - 1) / R;
+  }
+  while (hp.ev.size() < size_t(2 * nb + 2)) {
+    cudaEvent_t e;
+    DFR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    hp.ev.push_back(e);
+  }
+  auto h2d_rows = [&](int r0, int r1) {
+    return copy_rows(hp.d_src + int64_t(r0) * dsp, dsp, host_img + int64_t(r0) * host_pitch,
+                     host_pitch, W, r1 - r0, cudaMemcpyHostToDevice, hp.h2d);
+  };
+  // value and footprint rows leave on two streams (two copy engines can serve them at once)
+  auto d2h_rows = [&](int t0, int t1, cudaEvent_t ready) {
+    cudaError_t e = cudaStreamWaitEvent(hp.d2h, ready, 0);
+    if (e == cudaSuccess)
+      e = copy_rows(host_out + int64_t(t0) * out_pitch, out_pitch, hp.d_out + int64_t(t0) * dop,
+                    dop, out_w, t1 - t0, cudaMemcpyDeviceToHost, hp.d2h);
+    if (e == cudaSuccess && host_fp) {
+      e = cudaStreamWaitEvent(hp.d2h_fp, ready, 0);
+      if (e == cudaSuccess)
+        e = copy_rows(host_fp + int64_t(t0) * out_pitch, out_pitch, hp.d_fp + int64_t(t0) * dop,
+                      dop, out_w, t1 - t0, cudaMemcpyDeviceToHost, hp.d2h_fp);
+    }
+    return e;
+  };
+  auto finish = [&]() -> int {
+    DFR_CUDA(cudaStreamSynchronize(hp.d2h));
+    DFR_CUDA(cudaStreamSynchronize(hp.d2h_fp));
+    return DFR_OK;
+  };
+  if (!banded) {
+    DFR_CUDA(h2d_rows(0, H));
+    DFR_CUDA(cudaEventRecord(hp.ev[0], hp.h2d));
+    DFR_CUDA(cudaStreamWaitEvent(hp.comp, hp.ev[0], 0));
+    if (order == DFR_BSPLINE3) {
+      DFR_CUDA(launch_bspline_prefilter(hp.d_src, dsp, W, H, hp.d_src, dsp, hp.comp));
+    }
+    rc = dfr_reproject(src, tgt, hp.d_src, dsp, hp.d_out, hp.d_fp, dop, x0, y0, out_w, out_h,
+                       order, flags, nullptr, hp.comp);
+    if (rc != DFR_OK) return rc;
+    DFR_CUDA(cudaEventRecord(hp.ev[1], hp.comp));
+    DFR_CUDA(d2h_rows(0, out_h, hp.ev[1]));
+    return finish();
+  }
+  FwdLaunch L{};
+  L.total_tiles = P.cells_x * P.cells_y;
+  L.box_floats = box_floats(P);
+  const int nunits = (L.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
+  const int smem = smem_for(P);
+  std::vector<char> copied(size_t(H), 0);
+  for (int b = 0; b < nb; ++b) {
+    const int cr0 = b * R, cr1 = std::min(P.cells_y, cr0 + R);
+    const int t0 = cr0 * kCellH, t1 = std::min(out_h, cr1 * kCellH);
+    const int u0 = cr0 * P.cells_x / kCellsPerCta;
+    const int u1 = (b == nb - 1) ? nunits : cr1 * P.cells_x / kCellsPerCta;
+    int r0, r1;
+    band_source_rows(P, t0, t1, r0, r1);
+    // copy the rows of [r0, r1) that no earlier band copied, as contiguous runs
+    for (int r = r0; r < r1;) {
+      if (copied[size_t(r)]) {
+        ++r;
+        continue;
+      }
+      int e = r;
+      while (e < r1 && !copied[size_t(e)]) copied[size_t(e++)] = 1;
+      DFR_CUDA(h2d_rows(r, e));
+      r = e;
+    }
+    DFR_CUDA(cudaEventRecord(hp.ev[2 * b], hp.h2d));
+    DFR_CUDA(cudaStreamWaitEvent(hp.comp, hp.ev[2 * b], 0));
+    L.unit_begin = u0;
+    cudaError_t e = launch_forward(P, L, u1 - u0, forward_threads_default(), smem, hp.comp);
+    if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject_host launch");
+    DFR_CUDA(cudaEventRecord(hp.ev[2 * b + 1], hp.comp));
+    DFR_CUDA(d2h_rows(t0, t1, hp.ev[2 * b + 1]));
+  }
+  return finish();
 }
 
 extern "C" int dfr_bspline_prefilter(const float* img, int64_t pitch, int32_t w, int32_t h,

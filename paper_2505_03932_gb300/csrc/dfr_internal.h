@@ -90,6 +90,7 @@ struct FwdLaunch {
                              // tile_start[n])
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
   int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
+  int32_t unit_begin;        // single-frame split launch: first work unit (a band of the box)
 };
 
 // Backward launch arguments. The kernel accumulates parameter gradients in a padded layout

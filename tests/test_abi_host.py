@@ -257,3 +257,18 @@ def test_bspline_prefilter_argument_errors(dfr):
     assert L.dfr_bspline_prefilter(None, 64, 8, 10, d, 64, None) == -1
     assert L.dfr_bspline_prefilter(d, 4, 8, 10, e, 64, None) == -1
     assert L.dfr_bspline_prefilter(d, 64, 8, 10, d, 72, None) == -1  # in place, other stride
+
+
+def test_host_entry_argument_errors(dfr):
+    L = dfr.lib()
+    s = dfr.to_c(synth.tan_wcs(64, 48))
+    d = ctypes.c_void_p(16)
+    call = lambda **kw: L.dfr_reproject_host(
+        ctypes.byref(s), ctypes.byref(s), kw.get("img", d), kw.get("pitch", 64), kw.get("out", d),
+        None, kw.get("opitch", 64), 0, 0, kw.get("w", 64), kw.get("h", 48), kw.get("order", 1), 1)
+    assert call(w=0) == 0
+    assert call(w=-1) == -1
+    assert call(img=None) == -1
+    assert call(out=None) == -1
+    assert call(pitch=63) == -1
+    assert call(opitch=10) == -1
