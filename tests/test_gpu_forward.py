@@ -407,3 +407,38 @@ def test_tiny_and_odd_sources(shape, precision):
         e, fe = value_check(ref_img, order, val, fp, cr, precision)
         assert e <= VALUE_RTOL and fe <= 1e-6, (order, e, fe)
         assert (fp > 0).any(), order
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_large_frame_sampled(precision):
+    """A 20000x16000 source (SIP-3) onto a 24000x20000 bounding box (480 Mpix, about 5 GB on the
+    device: 64-bit output offsets, 469k anchor cells / 1.9M FP64 tiles in one launch), checked
+    on a seeded sample of 4000 pixels: coordinates against the FP64 oracle, values at the GPU's
+    coordinates, coverage decisions on the same numbers."""
+    T = torch()
+    rng = synth.rng_for(70)
+    W, H = 20000, 16000
+    src = synth.add_sip(synth.tan_wcs(W, H, scale_arcsec=1.0), 3, 1e-6, rng)
+    src, _ = OW.with_inverse_sip(src, 4)
+    tgt = synth.tan_wcs(24000, 20000, scale_arcsec=0.95, rho_deg=0.6,
+                        crpix=(12000.5 + 310.0, 10000.5 - 170.0))
+    img = (rng.standard_normal((H, W)) * 0.1).astype(np.float32)
+    img[:: 37, :: 41] += 50.0  # sparse bright points
+    bbox = (0, 0, 24000, 20000)
+    d = to_dev(img)
+    val, fp, cr = dfr().reproject(d, src, tgt, bbox=bbox, order="bicubic", precision=precision,
+                                  coords=True)
+    T.cuda.synchronize()
+    dfr().device_status()
+    px = T.from_numpy(rng.integers(0, 24000, 4000)).cuda()
+    py = T.from_numpy(rng.integers(0, 20000, 4000)).cuda()
+    v = val[py, px].cpu().numpy()
+    f = fp[py, px].cpu().numpy()
+    c = cr[py, px].cpu().numpy()
+    del val, fp, cr
+    ox, oy, ok = OR.coords(src, tgt, px.cpu().numpy(), py.cpu().numpy())
+    dd = np.hypot(c[:, 0] - ox, c[:, 1] - oy)[ok]
+    assert dd.max() < (FP64_PX if precision == "fp64" else SPLIT_PX)
+    e, fe = value_check(img, "bicubic", v[None], f[None], c[None], precision)
+    assert e <= VALUE_RTOL and fe <= 1e-6
+    assert (f > 0).mean() > 0.5 and (f == 0).any()
