@@ -78,44 +78,59 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HotPlan<ID
         const float g = B.grad_out[int64_t(oy + r) * B.go_pitch + gx];
         const float gF = __fdividef(g, F);
         if (B.grad_src) {
+          if (in_box) {
+            // every tap position is in the box; masked taps (outside the image) add 0 there
+            // and the flush skips them
 #pragma unroll
-          for (int k = 0; k < T::n; ++k)
+            for (int k = 0; k < T::n; ++k) {
+              const float gw = gF * wy[k];
+              float* row = gbox + (cy + k) * bw + cx;
 #pragma unroll
-            for (int q = 0; q < T::n; ++q) {
-              const float w = wx[q] * wy[k];
-              if (w == 0.f) continue;
-              if (in_box)
-                atomicAdd(gbox + (cy + k) * bw + (cx + q), gF * w);
-              else
-                atomicAdd(B.grad_src + int64_t(iy + k) * B.gs_pitch + (ix + q), gF * w);
+              for (int q = 0; q < T::n; ++q) atomicAdd(row + q, gw * wx[q]);
             }
+          } else {
+#pragma unroll
+            for (int k = 0; k < T::n; ++k)
+#pragma unroll
+              for (int q = 0; q < T::n; ++q) {
+                const float w = wx[q] * wy[k];
+                if (w != 0.f)
+                  atomicAdd(B.grad_src + int64_t(iy + k) * B.gs_pitch + (ix + q), gF * w);
+              }
+          }
         }
         if (want_params) {
-          float s[T::n][T::n];
-          float num = 0.f;
+          // value = sum_k wy_k row_k / F with row_k = sum_q wx_q S_kq; the position derivatives
+          // d(value)/dx = sum_k wy_k (sum_q dwx_q S_kq - value sum_q dwx_q) / F and
+          // d(value)/dy = sum_k dwy_k (row_k - value sum_q wx_q) / F
+          float row[T::n], rowd[T::n];
+          float num = 0.f, sdx = 0.f;
+#pragma unroll
+          for (int q = 0; q < T::n; ++q) sdx += dwx[q];
 #pragma unroll
           for (int k = 0; k < T::n; ++k) {
             const bool iny = unsigned(iy + k) < unsigned(Q.H);
-            float row = 0.f;
+            float rw = 0.f, rd = 0.f;
 #pragma unroll
             for (int q = 0; q < T::n; ++q) {
               const bool in = iny && unsigned(ix + q) < unsigned(Q.W);
-              s[k][q] = in_box ? box[(cy + k) * bw + (cx + q)]
-                               : (in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q)) : 0.f);
-              row = fmaf(wx[q], s[k][q], row);
+              const float sv = in_box ? box[(cy + k) * bw + (cx + q)]
+                                      : (in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q))
+                                            : 0.f);
+              rw = fmaf(wx[q], sv, rw);
+              rd = fmaf(dwx[q], sv, rd);
             }
-            num = fmaf(wy[k], row, num);
+            row[k] = rw;
+            rowd[k] = rd;
+            num = fmaf(wy[k], rw, num);
           }
           const float val = __fdividef(num, F);
           float ax_ = 0.f, ay_ = 0.f;
 #pragma unroll
-          for (int k = 0; k < T::n; ++k)
-#pragma unroll
-            for (int q = 0; q < T::n; ++q) {
-              const float d = s[k][q] - val;
-              ax_ = fmaf(dwx[q] * wy[k], d, ax_);
-              ay_ = fmaf(wx[q] * dwy[k], d, ay_);
-            }
+          for (int k = 0; k < T::n; ++k) {
+            ax_ = fmaf(wy[k], fmaf(-val, sdx, rowd[k]), ax_);
+            ay_ = fmaf(dwy[k], fmaf(-val, sx, row[k]), ay_);
+          }
           gxs = gF * ax_;
           gys = gF * ay_;
         }
@@ -168,7 +183,7 @@ __device__ __forceinline__ void flush_gbox(const HotPlan<IDEG, false>& Q, const 
 }
 
 template <int ORDER, int IDEG, int FD>
-__global__ void __launch_bounds__(kWarps * 32) bwd_split_kernel(const __grid_constant__ FwdPlan P,
+__global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_constant__ FwdPlan P,
                                                                 const __grid_constant__ BwdExtra B) {
   constexpr int NTERM = nterms(FD);
   constexpr int NP = 6 + 2 * NTERM;
