@@ -107,23 +107,39 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HotPlan<ID
           float num = 0.f, sdx = 0.f;
 #pragma unroll
           for (int q = 0; q < T::n; ++q) sdx += dwx[q];
+          // taps from the staged box (branch-free), else from global memory (masked)
+          if (in_box) {
+            const float* b0 = box + cy * bw + cx;
 #pragma unroll
-          for (int k = 0; k < T::n; ++k) {
-            const bool iny = unsigned(iy + k) < unsigned(Q.H);
-            float rw = 0.f, rd = 0.f;
+            for (int k = 0; k < T::n; ++k) {
+              float rw = 0.f, rd = 0.f;
 #pragma unroll
-            for (int q = 0; q < T::n; ++q) {
-              const bool in = iny && unsigned(ix + q) < unsigned(Q.W);
-              const float sv = in_box ? box[(cy + k) * bw + (cx + q)]
-                                      : (in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q))
-                                            : 0.f);
-              rw = fmaf(wx[q], sv, rw);
-              rd = fmaf(dwx[q], sv, rd);
+              for (int q = 0; q < T::n; ++q) {
+                const float sv = b0[k * bw + q];
+                rw = fmaf(wx[q], sv, rw);
+                rd = fmaf(dwx[q], sv, rd);
+              }
+              row[k] = rw;
+              rowd[k] = rd;
             }
-            row[k] = rw;
-            rowd[k] = rd;
-            num = fmaf(wy[k], rw, num);
+          } else {
+#pragma unroll
+            for (int k = 0; k < T::n; ++k) {
+              const bool iny = unsigned(iy + k) < unsigned(Q.H);
+              float rw = 0.f, rd = 0.f;
+#pragma unroll
+              for (int q = 0; q < T::n; ++q) {
+                const bool in = iny && unsigned(ix + q) < unsigned(Q.W);
+                const float sv = in ? __ldg(P.img + int64_t(iy + k) * P.pitch + (ix + q)) : 0.f;
+                rw = fmaf(wx[q], sv, rw);
+                rd = fmaf(dwx[q], sv, rd);
+              }
+              row[k] = rw;
+              rowd[k] = rd;
+            }
           }
+#pragma unroll
+          for (int k = 0; k < T::n; ++k) num = fmaf(wy[k], row[k], num);
           const float val = __fdividef(num, F);
           float ax_ = 0.f, ay_ = 0.f;
 #pragma unroll
