@@ -259,6 +259,10 @@ def run_gpu(args, rank, world, local_rank):
                            out=host_out, fp_out=host_fp)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
 
     peak, peak_src = _peaks()
     achieved = BYTES_PER_PIX * npix / (ms * 1e-3) / 1e9
