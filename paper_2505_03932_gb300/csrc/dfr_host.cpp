@@ -238,10 +238,6 @@ struct HostMap {
 
 }  // namespace
 
-// Exposed for the batch and backward paths in this file.
-struct PlanCtx {
-  dfr_wcs src, tgt;
-};
 
 static double horner_host(const double* c, int n, double u, double v) {
   double P = 0.0;
@@ -1710,6 +1706,5 @@ int plan_box_floats(const FwdPlan& P) { return box_floats(P); }
 int plan_smem_bytes(int floats) { return smem_for_floats(floats); }
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
 int report_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
-void prefix_error(const std::string& pfx) { g_err = pfx + g_err; }
 
 }  // namespace dfr
