@@ -43,7 +43,7 @@ extern "C" {
 #define DFR_OK                   0
 #define DFR_ERR_INVALID_ARG     -1  /* null/ill-sized argument, bad order or flag          */
 #define DFR_ERR_HEADER_PARSE    -2  /* malformed card or missing required keyword          */
-#define DFR_ERR_UNSUPPORTED_WCS -3  /* CTYPE not RA---TAN/DEC--TAN[-SIP], LONPOLE != 180   */
+#define DFR_ERR_UNSUPPORTED_WCS -3  /* CTYPE not RA---TAN/DEC--TAN[-SIP]                   */
 #define DFR_ERR_SINGULAR_CD     -4  /* det(CD) == 0 or non-finite                          */
 #define DFR_ERR_NO_INVERSE_SIP  -5  /* source has A/B but no AP/BP and no exact inverse    */
 #define DFR_ERR_CUDA            -6  /* a CUDA runtime call failed                          */

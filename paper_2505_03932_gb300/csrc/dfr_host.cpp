@@ -1571,6 +1571,7 @@ extern "C" int dfr_bspline_prefilter(const float* img, int64_t pitch, int32_t w,
   if (pitch < w || coef_pitch < w) return fail(DFR_ERR_INVALID_ARG, "pitch < width");
   if (img == coef && pitch != coef_pitch)
     return fail(DFR_ERR_INVALID_ARG, "in-place prefilter needs equal strides");
+  std::lock_guard<std::mutex> lock(g_mu);  // the scratch image is one buffer per device
   cudaError_t e = launch_bspline_prefilter(img, pitch, w, h, coef, coef_pitch,
                                            static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_bspline_prefilter launch");
