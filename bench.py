@@ -212,7 +212,9 @@ def run_gpu(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the timed region
-    step()
+    for _ in range(max(args.warmup, 3)):  # the GPU idled during the sleep: warm up again
+        flush.fill_(1.0)
+        step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     times = timed(args.steps, "split")
