@@ -206,15 +206,15 @@ def run_gpu(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     dfr.device_status()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     clocks = Clocks(local_rank)
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the timed region
     for _ in range(max(args.warmup, 3)):  # the GPU idled during the sleep: warm up again
         flush.fill_(1.0)
         step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     times = timed(args.steps, "split")
