@@ -12,7 +12,8 @@ over the whole frame. Inputs are synthetic (seeded sky noise + 2000 Gaussian sta
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the launching
 stream, with a 512 MB write between steps to flush the 129 MB L2 (the flush is outside the
 events); barrier + synchronize around the timed loop; max over ranks. The reference arm
-(--impl reference) times the FP64 CPU oracle on a bounded pixel sample of the same workload.
+(--impl reference) times the FP64 CPU oracle on a bounded pixel sample of the same workload, on
+every host core (one spawned process per core).
 """
 from __future__ import annotations
 
@@ -144,15 +145,73 @@ def oracle_wcs(src):
     return w
 
 
+_WORKER = {}
+
+
+def _oracle_worker_init(barrier):
+    """Pool initializer: each worker builds the seeded workload itself (about 1 s), then waits
+    until every worker has, so that no start-up time falls inside a timed map."""
+    src, tgt, img = workload()
+    _WORKER["args"] = (oracle_wcs(src), tgt, img)
+    barrier.wait(timeout=600)
+
+
+def _oracle_worker_run(task):
+    npix, seed = task
+    return oracle_sample_rate(*_WORKER["args"], npix, seed=seed)
+
+
+class OraclePool:
+    """The oracle run on every host core: one spawned process per core, each evaluating its own
+    share of random target pixels (rows of work split statically, like OpenMP static rows)."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0))
+        ctx = mp.get_context("spawn")
+        # one thread per worker process: the workers inherit these at spawn
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ.update({k: "1" for k in saved})
+        try:
+            self.pool = ctx.Pool(self.cores, initializer=_oracle_worker_init,
+                                 initargs=(ctx.Barrier(self.cores),))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        # returns once every worker is past the barrier (bounded: a worker that fails to start
+        # is replaced by the pool and would otherwise leave the map waiting)
+        self._map([(1000, k) for k in range(self.cores)], timeout=600)
+
+    def _map(self, tasks, timeout):
+        return self.pool.map_async(_oracle_worker_run, tasks, chunksize=1).get(timeout=timeout)
+
+    def seconds(self, npix_per_core, seed):
+        """Wall seconds for cores x npix_per_core pixels."""
+        tasks = [(npix_per_core, seed * 1000 + k) for k in range(self.cores)]
+        t0 = time.perf_counter()
+        self._map(tasks, timeout=600)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    src, tgt, img = workload()
-    src = oracle_wcs(src)
-    npix = 1_000_000  # about 1 s of one core per step
-    for _ in range(args.warmup):
-        oracle_sample_rate(src, tgt, img, npix // 4)
-    secs = [oracle_sample_rate(src, tgt, img, npix, seed=100 + k) for k in range(args.steps)]
+    pool = OraclePool()
+    try:
+        per_core = 250_000  # about 0.25 s of each core per step
+        for k in range(args.warmup):
+            pool.seconds(per_core // 4, seed=1 + k)
+        secs = [pool.seconds(per_core, seed=100 + k) for k in range(args.steps)]
+    finally:
+        pool.close()
+    npix = per_core * pool.cores
     t = float(np.mean(secs))
     mpix = npix / t / 1e6
     line = {
@@ -161,8 +220,9 @@ def run_reference(args, rank, world):
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_pixels_per_step": npix},
-        "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d random target pixels of the 4096^2 frame per step" % npix},
+        "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": "%d random target pixels of the 4096^2 frame per step, "
+                                   "%d per core" % (npix, per_core)},
         "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -274,10 +334,20 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         o_src = oracle_wcs(src_rec)
-        npx = 12_000_000  # about 10 s of one core
-        secs = oracle_sample_rate(o_src, tgt_rec, img, npx)
-        cpu = {"value": npx / secs / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-               "sample": "%d random target pixels of the 4096^2 frame (%.1f s)" % (npx, secs)}
+        npx1 = 3_000_000  # about 3 s of one core
+        secs1 = oracle_sample_rate(o_src, tgt_rec, img, npx1)
+        pool = OraclePool()
+        try:
+            per_core = 1_500_000  # about 1.5 s of each core
+            secs = pool.seconds(per_core, seed=7)
+        finally:
+            pool.close()
+        npx = per_core * pool.cores
+        cpu = {"value": npx / secs / 1e6, "unit": "Mpix/s", "cores": pool.cores, "kind": "oracle",
+               "sample": "%d random target pixels of the 4096^2 frame, %d per core (%.1f s)"
+                         % (npx, per_core, secs),
+               "single_core": {"value": npx1 / secs1 / 1e6, "unit": "Mpix/s",
+                               "sample": "%d random target pixels (%.1f s)" % (npx1, secs1)}}
 
     if rank == 0:
         line = {
