@@ -3,8 +3,9 @@
 
 Workload (the bench step): one 4096x4096 float32 exposure, TAN-SIP order 3 with AP/BP order 4
 (fitted by the library), reprojected with bicubic interpolation onto a 4096x4096 TAN target
-rotated 1.2 deg, offset (41.3, -17.9) px, 1% larger pixels; split precision (FP64 sky rotation
-at per-tile anchors, FP32 per pixel); value and footprint written. One step = one fused launch
+rotated 1.2 deg, offset (41.3, -17.9) px, 1% larger pixels; split precision (the sky rotation at
+one anchor per 32x32 cell in double-float arithmetic, FP32 per pixel); value and footprint
+written. One step = one fused launch
 over the whole frame. Inputs are synthetic (seeded sky noise + 2000 Gaussian stars).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]

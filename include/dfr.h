@@ -60,7 +60,7 @@ extern "C" {
 
 /* flags */
 #define DFR_FP64           0u  /* all-FP64 per pixel: the printed formulas, with libm trig   */
-#define DFR_SPLIT          1u  /* FP64 sky rotation at per-tile anchors, FP32 per pixel      */
+#define DFR_SPLIT          1u  /* sky rotation at per-cell anchors (~48 bit), FP32 per pixel */
 #define DFR_EXACT_INVERSE  2u  /* source inverse = Newton solve of A/B (AP/BP as start)      */
 #define DFR_NO_TMA         4u  /* gather straight from global memory instead of TMA tiles    */
 #define DFR_NAN_MASK       8u  /* NaN source pixels are missing: no weight in value or        */

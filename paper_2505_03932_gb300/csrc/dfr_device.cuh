@@ -389,8 +389,9 @@ __device__ __forceinline__ bool source_from_target_fp64(const FwdPlan& P, double
 }
 
 // ---------------------------------------------------------------- split-precision anchor
-// FP64 part of the split path, once per 64x16 tile: the homography at the tile's anchor
-// pixel and the FP32 coefficients of its local expansion.
+// Wide-precision part of the split path, once per 32x32 cell: the homography at the cell's
+// anchor pixel (double-float, or FP64 with a target SIP), the anchor's source position split
+// into integer and fractional parts, and the FP32 coefficients of the local expansion.
 struct Anchor {
   int32_t bx, by;        // integer part of the anchor's source position
   int32_t ax, ay;        // anchor target pixel (absolute)
@@ -420,6 +421,85 @@ __device__ __forceinline__ void tsip_pair(const FwdPlan& P, float u, float v, fl
   }
 }
 
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two floats with |lo| at
+// most half an ulp of hi (about 48 significant bits). Error-free transformations: Knuth's
+// TwoSum, the fast form of Dekker's sum (|a| >= |b|) and the FMA form of Dekker's product;
+// the addition is the accurate one (both parts summed with TwoSum). Every step is an
+// explicitly rounded intrinsic, so no contraction or reassociation can change a result
+// between the kernels that build anchors.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_quick_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = ff_two_sum(a.hi, b.hi);
+  const FF t = ff_two_sum(a.lo, b.lo);
+  s = ff_quick_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return ff_quick_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_quick_sum(p, e);
+}
+__device__ __forceinline__ FF ff_load(const float* hl) { return {hl[0], hl[1]}; }
+
+// Anchor without target SIP, in double-float on the FP32 pipes (the FP64 pipe is narrow on
+// this part and the anchor is a chain of dependent operations): the homography numerators
+// and denominator at the anchor, 1 / h2 by one Newton step from the FP32 reciprocal (24 -> 48
+// bits), the source position and its split into integer and fractional parts.
+__device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, int ax, int ay, Anchor& a) {
+  const FF u = ff_add(FF{float(ax), 0.f}, ff_neg(ff_load(P.crpix_t_ff[0])));
+  const FF v = ff_add(FF{float(ay), 0.f}, ff_neg(ff_load(P.crpix_t_ff[1])));
+  a.tu = u.hi;
+  a.tv = v.hi;
+  a.tA = a.tB = 0.f;
+  FF h[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    h[i] = ff_add(ff_add(ff_mul(ff_load(P.G_ff[i][0]), u), ff_mul(ff_load(P.G_ff[i][1]), v)),
+                  ff_load(P.G_ff[i][2]));
+  const float r0 = __frcp_rn(h[2].hi);
+  const FF e = ff_add(FF{1.f, 0.f}, ff_neg(ff_mul(h[2], FF{r0, 0.f})));
+  const FF r = ff_add(FF{r0, 0.f}, ff_mul(FF{r0, 0.f}, e));
+  const FF U0 = ff_mul(h[0], r), V0 = ff_mul(h[1], r);
+  const float U0f = U0.hi, V0f = V0.hi;
+  const float g20 = P.G_ff[2][0][0], g21 = P.G_ff[2][1][0];
+  a.a0 = fmaf(-U0f, g20, P.G_ff[0][0][0]);
+  a.a1 = fmaf(-U0f, g21, P.G_ff[0][1][0]);
+  a.b0 = fmaf(-V0f, g20, P.G_ff[1][0][0]);
+  a.b1 = fmaf(-V0f, g21, P.G_ff[1][1][0]);
+  a.g20 = g20;
+  a.g21 = g21;
+  a.h2 = h[2].hi;
+  a.U0 = U0f;
+  a.V0 = V0f;
+  const FF X0 = ff_add(U0, ff_load(P.crpix_s_ff[0]));
+  const FF Y0 = ff_add(V0, ff_load(P.crpix_s_ff[1]));
+  // floor of hi + lo: floor(hi), one less when hi is an integer and lo < 0; exact while
+  // |hi| < 2^24, and anchors farther out than that leave their cell uncovered
+  const bool finite = fabsf(X0.hi) < 16777216.f && fabsf(Y0.hi) < 16777216.f;
+  float fx = floorf(X0.hi), fy = floorf(Y0.hi);
+  if (X0.hi == fx && X0.lo < 0.f) fx = __fsub_rn(fx, 1.f);
+  if (Y0.hi == fy && Y0.lo < 0.f) fy = __fsub_rn(fy, 1.f);
+  a.bx = finite ? int32_t(fx) : 0;
+  a.by = finite ? int32_t(fy) : 0;
+  a.f0x = finite ? __fadd_rn(__fsub_rn(X0.hi, fx), X0.lo) : 0.f;
+  a.f0y = finite ? __fadd_rn(__fsub_rn(Y0.hi, fy), Y0.lo) : 0.f;
+  if (!finite || !(h[2].hi > 0.f)) a.h2 = -1.f;  // the whole cell is treated as uncovered
+}
+
 __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
   a.ax = ax;
   a.ay = ay;
@@ -436,8 +516,12 @@ __device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, An
     a.tu = a.tv = a.tA = a.tB = 0.f;
     return;
   }
-  // FP64 only where absolute positions need it: the homography at the anchor and the anchor's
-  // source position; the local expansion coefficients follow in FP32
+  if (P.tsip_deg <= 0) {
+    make_anchor_ff(P, ax, ay, a);
+    return;
+  }
+  // with target SIP: FP64 where absolute positions need it (the target SIP, the homography at
+  // the anchor and the anchor's source position); the local expansion follows in FP32
   const double u = __dsub_rn(double(ax), P.crpix_t[0]);
   const double v = __dsub_rn(double(ay), P.crpix_t[1]);
   double p = u, q = v;

@@ -146,7 +146,7 @@ __device__ __forceinline__ void prefetch_sums(const HotPlan<IDEG, PAIRS>& Q, int
 
 // ------------------------------------------------------------------ split-precision tiles
 // One warp owns a 32x8 tile at a time: lane = column, 8 rows per lane. Per pixel the source
-// position comes in FP32 from the FP64 anchor of the pixel's 32x32 cell; per tile a TMA load
+// position comes in FP32 from the anchor of the pixel's 32x32 cell; per tile a TMA load
 // stages the source box covering the tile's taps in the warp's shared buffer.
 
 // Value and footprint of one pixel from its taps. S(k, q) reads tap (row k, column q) and must
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
 // coefficients held in registers as FP32x2 pairs; otherwise one frame whose plan is the kernel
 // parameter, read as constant-bank operands by scalar FMAs (fewer registers).
 //
-// Work unit: kCellsPerCta consecutive 32x32 anchor cells. Warp 0 computes their FP64 anchors
+// Work unit: kCellsPerCta consecutive 32x32 anchor cells. Warp 0 computes their anchors
 // (one lane per cell), then each warp processes the 4 tiles of each of its kCellsPerWarp cells,
 // requesting the source box of the next tile before gathering the current one.
 template <int ORDER, int IDEG, bool BATCH, bool ACC, bool TSIP = false>
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP
   while (unit < nunits) {
     const int c0 = unit * kCellsPerCta;
     const int nc = min(kCellsPerCta, total - c0);
-    if (warp == 0 && lane < nc) {  // FP64 anchors of the unit's cells, one per lane
+    if (warp == 0 && lane < nc) {  // anchors of the unit's cells, one per lane
       int f = 0, cell = c0 + lane;
       if (batch) {
         f = frame_of(L, cell);

@@ -461,6 +461,17 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
       for (int j = 0; j < 3; ++j) P.G[i][j] = G[i][j] / g22;
   }
 
+  auto split_ff = [](double d, float* hl) {
+    hl[0] = float(d);
+    hl[1] = float(d - double(hl[0]));
+  };
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) split_ff(P.G[i][j], P.G_ff[i][j]);
+  for (int i = 0; i < 2; ++i) {
+    split_ff(P.crpix_t[i], P.crpix_t_ff[i]);
+    split_ff(P.crpix_s[i], P.crpix_s_ff[i]);
+  }
+
   // TMA staging of the source tile (split path only)
   P.use_tma = 0;
   if ((flags & DFR_SPLIT) && !(flags & DFR_NO_TMA) && w > 0 && h > 0) {

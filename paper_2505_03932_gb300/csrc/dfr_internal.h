@@ -23,9 +23,10 @@ __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) /
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
-// Anchor cell of the split path: 32 x 32 pixels (four tiles stacked in y), one FP64 anchor at
-// its centre. A CTA of kWarps warps takes kCellsPerCta consecutive cells; their anchors are
-// computed together, one per lane, then each warp processes the tiles of kCellsPerWarp cells.
+// Anchor cell of the split path: 32 x 32 pixels (four tiles stacked in y), one anchor (about
+// 48-bit double-float arithmetic; FP64 with a target SIP) at its centre. A CTA of kWarps warps
+// takes kCellsPerCta consecutive cells; their anchors are computed together, one per lane, then
+// each warp processes the tiles of kCellsPerWarp cells.
 constexpr int kCellW = 32;
 constexpr int kCellH = 32;
 constexpr int kTilesPerCell = kCellH / kTileH;
@@ -60,6 +61,12 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   // split path: homography from target intermediate offsets (p, q) (after SIP, pixels) to
   // source intermediate offsets (U, V) (before inverse SIP, pixels), scaled so G[2][2] = 1
   double G[3][3];
+  // the same G, CRPIX - 1 of the target and of the source as unevaluated float pairs
+  // (hi, lo; hi = the nearest float, lo = the nearest float to the rest) for the
+  // double-float arithmetic of the split path's anchors
+  float G_ff[3][3][2];
+  float crpix_t_ff[2][2];
+  float crpix_s_ff[2][2];
   // source WCS
   double crpix_s[2];         // CRPIX - 1
   int32_t isip_deg;          // packed degree of AP, BP (0 = none)

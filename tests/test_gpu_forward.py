@@ -190,7 +190,7 @@ def test_far_tangent_points_and_target_sip():
 def test_source_far_hemisphere_is_uncovered():
     """A wide target grid whose tangent point is 80 deg from the source's: pixels whose sky
     position lies on the far hemisphere of the source projection are uncovered. The FP64 path
-    decides per pixel exactly like the oracle; the split path (FP64 anchor per tile) never
+    decides per pixel exactly like the oracle; the split path (one wide-precision anchor per cell) never
     covers such a pixel."""
     src = synth.tan_wcs(64, 64, crval=(0.0, 0.0))
     tgt = synth.tan_wcs(64, 64, crval=(80.0, 0.0), scale_arcsec=3600.0 * 3)  # 3 deg/px
