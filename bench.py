@@ -105,22 +105,39 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the bench kernel from the committed ncu summary, or None when the
-    kernel source has changed since those counters were taken."""
+def _recorded():
+    """Counters of the bench kernel from the committed ncu summary (key: value lines), or {} when
+    the kernel source has changed since those counters were taken."""
     path = os.path.join(ROOT, "profiles", "split_bicubic_4096.md")
     try:
         rec = {}
         for line in open(path):
-            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch",
-                                                      "kernel_source_sha256"):
-                k, v = line.split(":", 1)
+            k, sep, v = line.partition(":")
+            if sep and k in ("traffic_bytes_per_launch", "kernel_source_sha256",
+                             "issue_ipc", "instructions_per_pixel"):
                 rec[k] = v.strip()
         if rec.get("kernel_source_sha256") == kernel_source_hash():
-            return int(rec["traffic_bytes_per_launch"])
+            return rec
     except Exception:
         pass
-    return None
+    return {}
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the bench kernel (ncu), or None (kernel changed since)."""
+    rec = _recorded()
+    return int(rec["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in rec else None
+
+
+def recorded_issue():
+    """The bench kernel's instruction issue rate from the same capture: the kernel is bound by
+    instruction issue (4 per SM per cycle), not by HBM; None when the kernel changed since."""
+    rec = _recorded()
+    if "issue_ipc" not in rec:
+        return None
+    ipc = float(rec["issue_ipc"])
+    return {"ipc": ipc, "peak_ipc": 4.0, "frac": ipc / 4.0,
+            "instructions_per_pixel": float(rec["instructions_per_pixel"]), "source": "ncu"}
 
 
 def workload():
@@ -362,6 +379,7 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "issue": recorded_issue(),
                          "peak_source": peak_src,
                          "bytes_per_pixel": BYTES_PER_PIX},
             "fp64_path": {"ms_per_step": ms64, "value": npix / (ms64 * 1e-3) / 1e6,
