@@ -113,6 +113,18 @@ def sqrt(a):
     return _unary(a, np.sqrt, lambda x: 0.5 / np.sqrt(x))
 
 
+def sinc(a):
+    """numpy's normalised sinc, sin(pi x) / (pi x), with derivative (cos(pi x) - sinc(x)) / x;
+    below |x| = 1e-3 the derivative's Taylor series -pi^2 x / 3 + pi^4 x^3 / 30 (the closed
+    form cancels there)."""
+    def fprime(x):
+        small = np.abs(x) < 1e-3
+        xs = np.where(small, 1.0, x)
+        series = -np.pi ** 2 * x / 3.0 + np.pi ** 4 * x ** 3 / 30.0
+        return np.where(small, series, (np.cos(np.pi * xs) - np.sinc(xs)) / xs)
+    return _unary(a, np.sinc, fprime)
+
+
 def arcsin(a):
     return _unary(a, np.arcsin, lambda x: 1.0 / np.sqrt(1.0 - x * x))
 
@@ -216,6 +228,12 @@ def _interp_dual(img, x, y, order, valid, a=-0.5):
         t = c - i0  # Dual
         if order == _interp.BILINEAR:
             return i0.astype(np.int64), [1.0 - t, t]
+        if order == _interp.LANCZOS3:
+            # L(d) = sinc(d) sinc(d / 3) at d = t + 2 - k, k = 0..5, divided by their sum
+            L = [sinc(t + float(2 - k)) * sinc((t + float(2 - k)) * (1.0 / 3.0))
+                 for k in range(6)]
+            tot = L[0] + L[1] + L[2] + L[3] + L[4] + L[5]
+            return (i0 - 2).astype(np.int64), [Lk / tot for Lk in L]
         aa = a
         # Keys kernel for the four taps at distances t+1, t, 1-t, 2-t, as polynomials in t
         w0 = aa * t * (t - 1.0) * (t - 1.0)
@@ -249,7 +267,7 @@ def _interp_dual(img, x, y, order, valid, a=-0.5):
 def reproject_dual(src, tgt, img, xt, yt, order, inverse="newton"):
     """Dual-valued output of the reprojection at target pixels (xt, yt), with derivatives
     with respect to the source WCS parameters (param_names order)."""
-    order = {"nearest": 0, "bilinear": 1, "bicubic": 2}.get(order, order)
+    order = {"nearest": 0, "bilinear": 1, "bicubic": 2, "lanczos3": 3}.get(order, order)
     ra, dec = _wcs.pix2world(tgt, np.asarray(xt, np.float64), np.asarray(yt, np.float64))
     dsrc, names = dual_wcs(src)
     import oracle.dual as m

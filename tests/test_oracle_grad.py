@@ -74,7 +74,26 @@ def fd_steps(src, tgt, px=1e-6):
     return px / np.maximum(mx, 1e-300)
 
 
-@pytest.mark.parametrize("order", ["bilinear", "bicubic"])
+def test_dual_sinc_derivative_matches_fd():
+    """The dual sinc's derivative (closed form, and its series below |x| = 1e-3) against FP64
+    central differences of numpy's sinc, across the series boundary and at the nodes."""
+    for x0 in (0.0, 1e-7, -4e-4, 9.99e-4, 1.001e-3, -0.3, 1.0, 2.7, -3.0):
+        d = D.sinc(D.Dual(np.array([x0]), np.array([[1.0]])))
+        h = 1e-5
+        fd = (np.sinc(x0 + h) - np.sinc(x0 - h)) / (2 * h)
+        assert abs(d.v[0] - np.sinc(x0)) == 0.0
+        assert abs(d.d[0, 0] - fd) < 1e-9, (x0, d.d[0, 0], fd)
+
+
+def test_dual_lanczos3_values_match_plain_oracle():
+    src, tgt, img, _ = _small_case("lanczos3")
+    Y, X = np.mgrid[0:96, 0:96].astype(np.float64)
+    o, _ = D.reproject_dual(src, tgt, img, X.ravel(), Y.ravel(), "lanczos3")
+    val, _, _, _ = R.reproject(src, tgt, img, "lanczos3", inverse="newton", use_snap=False)
+    np.testing.assert_allclose(o.v, val.ravel(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", ["bilinear", "bicubic", "lanczos3"])
 def test_loss_gradient_matches_central_fd(order):
     src, tgt, img, ref = _small_case(order)
     loss, grad, names = D.loss_grad(src, tgt, img, ref, order)

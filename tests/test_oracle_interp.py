@@ -125,7 +125,7 @@ def test_matches_scipy_map_coordinates(order):
     np.testing.assert_allclose(fp[inner], 1.0, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC])
+@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC, I.LANCZOS3])
 def test_adjoint_dot_product_and_dense(order):
     """<W s, g> = <s, W^T g> to 1e-12, and W built column by column from unit images equals the
     transpose built by the adjoint from unit gradients (brute force, 16x16)."""
