@@ -54,7 +54,7 @@ extern "C" {
 #define DFR_NEAREST  0
 #define DFR_BILINEAR 1
 #define DFR_BICUBIC  2   /* Keys cubic convolution, a = -0.5 */
-#define DFR_LANCZOS3 3   /* Lanczos-3 (6x6 taps, weights normalised per axis); forward only */
+#define DFR_LANCZOS3 3   /* Lanczos-3 (6x6 taps, weights normalised per axis)               */
 #define DFR_BSPLINE3 4   /* cubic B-spline on prefiltered coefficients (dfr_bspline_prefilter), */
                          /* mirror boundary, footprint 1 where covered; forward only           */
 
@@ -221,7 +221,9 @@ int dfr_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch, 
  *    A_pq for 1 <= p+q <= A_ORDER (by p+q, then p descending), B_pq likewise],
  * i.e. 6 + n_terms(A) + n_terms(B) doubles. The paper has no gradient; this extension lets
  * alignment parameters be fitted by gradient descent. Source positions use the same
- * arithmetic as the forward call with the same flags. Asynchronous on `stream`. */
+ * arithmetic as the forward call with the same flags. order: DFR_NEAREST, DFR_BILINEAR,
+ * DFR_BICUBIC or DFR_LANCZOS3; DFR_BSPLINE3 and the DFR_NAN_MASK flag are refused
+ * (DFR_ERR_INVALID_ARG). Asynchronous on `stream`. */
 int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                            const float* src_img, int64_t src_pitch,
                            const float* grad_out, int64_t go_pitch,

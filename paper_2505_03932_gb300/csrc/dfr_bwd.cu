@@ -259,7 +259,7 @@ static const void* bwd_for_order(int fd) {
 // degree <= 5 (its per-lane accumulators: 6 + 2 * 20 registers); the per-pixel kernel serves
 // the rest (FP64 path, degree 9, sources without a tensor map).
 static bool staged(const FwdPlan& p0, int fd) {
-  return (p0.flags & DFR_SPLIT) && p0.use_tma && fd <= 5;
+  return (p0.flags & DFR_SPLIT) && p0.use_tma && fd <= 5 && p0.order != DFR_LANCZOS3;
 }
 
 static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
@@ -267,6 +267,7 @@ static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
   switch (p0.order) {
     case DFR_NEAREST: return bwd_for_order<DFR_NEAREST>(fd);
     case DFR_BILINEAR: return bwd_for_order<DFR_BILINEAR>(fd);
+    case DFR_LANCZOS3: return bwd_for_order<DFR_LANCZOS3>(fd);
     default: return bwd_for_order<DFR_BICUBIC>(fd);
   }
 }

@@ -275,6 +275,61 @@ __device__ __forceinline__ void weights2(float2 t, float2* w) {
   }
 }
 
+// d/dt of the normalised Lanczos-3 weights. In the form of lanczos3_weights, each unnormalised
+// weight times t: v_k = (-1)^k a_k(th) t / d_k^2 for k != 2 and v_2 = sin(th) / t (finite at
+// t = 0), th = pi t / 3, a_k the angle-addition terms, a_k' their derivatives in th. Then
+// dv_k/dt = (-1)^k (pi/3 a_k' t + a_k (1 - 2 t / d_k)) / d_k^2, and for k = 2, with
+// sin(th) / t = (pi/3) sin(th) / th, dv_2/dt = (pi/3)^2 (th cos th - sin th) / th^2, by its
+// series -th / 3 + th^3 / 30 below th = 0.05 (the closed form cancels there). The normalised
+// weights w = v / S (S = sum v) have dw_k/dt = (dv_k - w_k sum dv) / S. The kernel is even, so
+// w_k(t) = w_{5-k}(1 - t): above t = 1/2 the derivatives come from 1 - t, mirrored, so that the
+// node nearest t is always k = 2 (where the series keeps the pole out of the arithmetic).
+template <typename T>
+__device__ __forceinline__ void lanczos3_dweights(T t_in, T* d) {
+  const bool mirror = t_in > T(0.5);
+  const T t = mirror ? T(1) - t_in : t_in;
+  const T pi3 = T(1.04719755119659774615);  // pi / 3
+  const T th = pi3 * t;
+  T s, c;
+  sincospi_t(t / T(3), &s, &c);
+  const T h = T(0.86602540378443864676);  // sin(pi / 3)
+  const T a[6] = {fma(c, h, T(-0.5) * s), fma(c, h, T(0.5) * s), s,
+                  fma(-c, h, T(0.5) * s), fma(-c, h, T(-0.5) * s), -s};
+  const T ad[6] = {fma(-s, h, T(-0.5) * c), fma(-s, h, T(0.5) * c), c,
+                   fma(s, h, T(0.5) * c), fma(s, h, T(-0.5) * c), -c};
+  T v[6], dv[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    if (k == 2) continue;
+    const T dk = t + T(2 - k);
+    const T sg = (k & 1) ? T(-1) : T(1);
+    const T inv2 = T(1) / (dk * dk);
+    v[k] = sg * a[k] * t * inv2;
+    dv[k] = sg * fma(pi3 * ad[k], t, a[k] * (T(1) - T(2) * t / dk)) * inv2;
+  }
+  if (th < T(0.05)) {
+    const T th2 = th * th;
+    v[2] = pi3 * fma(th2, fma(th2, T(1.0 / 120.0), T(-1.0 / 6.0)), T(1));
+    dv[2] = pi3 * pi3 * th * fma(th2, T(1.0 / 30.0), T(-1.0 / 3.0));
+  } else {
+    v[2] = s / t;
+    dv[2] = pi3 * pi3 * (th * c - s) / (th * th);
+  }
+  T S = T(0), Sd = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    S += v[k];
+    Sd += dv[k];
+  }
+  const T inv = T(1) / S;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int j = mirror ? 5 - k : k;
+    const T dk = (dv[j] - v[j] * inv * Sd) * inv;
+    d[k] = mirror ? -dk : dk;
+  }
+}
+
 // d(weights)/dt for the backward pass.
 template <int ORDER, typename T>
 __device__ __forceinline__ void dweights(T t, T* d) {
@@ -283,6 +338,8 @@ __device__ __forceinline__ void dweights(T t, T* d) {
   } else if (ORDER == DFR_BILINEAR) {
     d[0] = T(-1);
     d[1] = T(1);
+  } else if (ORDER == DFR_LANCZOS3) {
+    lanczos3_dweights<T>(t, d);
   } else {
     const T s = T(1) - t;
     // w0 = -t s^2 / 2          -> -(s^2)/2 + t s

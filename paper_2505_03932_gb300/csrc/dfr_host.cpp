@@ -1612,9 +1612,8 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                                       double* grad_params, void* stream) {
   if (flags & DFR_NAN_MASK)
     return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK is not supported by the adjoint");
-  if (order == DFR_LANCZOS3 || order == DFR_BSPLINE3)
-    return fail(DFR_ERR_INVALID_ARG, "%s is not supported by the adjoint",
-                order == DFR_LANCZOS3 ? "DFR_LANCZOS3" : "DFR_BSPLINE3");
+  if (order == DFR_BSPLINE3)
+    return fail(DFR_ERR_INVALID_ARG, "DFR_BSPLINE3 is not supported by the adjoint");
   FwdPlan P;
   // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
   // split path stages source and gradient boxes by tile, as sized by the plan

@@ -239,13 +239,13 @@ def test_adjoint_refuses_the_nan_mask_flag(dfr):
     assert rc == -1 and "NAN_MASK" in L.dfr_last_error().decode()
 
 
-def test_adjoint_refuses_lanczos3(dfr):
+def test_adjoint_refuses_bspline3(dfr):
     L = dfr.lib()
     s = dfr.to_c(synth.tan_wcs(64, 64))
     rc = L.dfr_reproject_backward(ctypes.byref(s), ctypes.byref(s), ctypes.c_void_p(16), 64,
-                                  ctypes.c_void_p(16), 64, 0, 0, 64, 64, dfr.LANCZOS3, dfr.SPLIT,
+                                  ctypes.c_void_p(16), 64, 0, 0, 64, 64, dfr.BSPLINE3, dfr.SPLIT,
                                   None, 0, None, None)
-    assert rc == -1 and "LANCZOS3" in L.dfr_last_error().decode()
+    assert rc == -1 and "BSPLINE3" in L.dfr_last_error().decode()
 
 
 def test_bspline_prefilter_argument_errors(dfr):

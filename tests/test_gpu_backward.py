@@ -51,7 +51,7 @@ def _group_check(grad, ref, names):
     return worst
 
 
-@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic"])
+@pytest.mark.parametrize("order", ["nearest", "bilinear", "bicubic", "lanczos3"])
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_grad_src_matches_oracle_adjoint(order, precision):
     src, tgt, img, _ = _case(order=order)
@@ -77,7 +77,7 @@ def test_grad_src_matches_oracle_adjoint(order, precision):
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1.0) * 10
 
 
-@pytest.mark.parametrize("order", ["bilinear", "bicubic"])
+@pytest.mark.parametrize("order", ["bilinear", "bicubic", "lanczos3"])
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_param_gradients_match_dual_numbers(order, precision):
     src, tgt, img, ref = _case(order=order)
