@@ -419,6 +419,62 @@ def _events_time(fn, k, flush=None):
     return float(np.median(ts)), float(np.median(hs))
 
 
+def run_oracle(args):
+    """The FP64 CPU oracle, as it stands, in one process on each configuration (no GPU):
+    whole frames for the 512^2 and 2048^2 cases, 1M random pixels of the 4096^2 frame, and a
+    seeded 1 % sample of every frame's bounding box for the two batches (Mpix/s of the sample,
+    which extrapolates to the whole batch). One JSON line per configuration."""
+    from oracle import reproject as OR
+    from oracle import wcs as OW
+    host = {"cores": 1, "host_cpus": len(os.sched_getaffinity(0)), "machine": os.uname().machine}
+
+    def timed(src, tgt, img, X, Y, order, inverse):
+        t0 = time.perf_counter()
+        OR.reproject_pixels(src, tgt, img, X, Y, order, inverse=inverse)
+        return time.perf_counter() - t0
+
+    def line(name, npx, secs, sample):
+        print(json.dumps(dict({"workload": name, "oracle_mpix_s": npx / secs / 1e6,
+                               "pixels": int(npx), "seconds": secs, "sample": sample}, **host)),
+              flush=True)
+
+    c = synth.config0()
+    Y, X = np.mgrid[0:512, 0:512].astype(np.float64)
+    line("512^2 TAN bilinear (config 0)", X.size,
+         timed(c["src"][0], c["tgt"], c["images"][0], X.ravel(), Y.ravel(), "bilinear", "poly"),
+         "whole frame")
+    src, tgt, img = workload()
+    src = oracle_wcs(src)
+    rng = synth.rng_for(7)
+    n1 = 1_000_000
+    X = rng.integers(0, 4096, n1).astype(np.float64)
+    Y = rng.integers(0, 4096, n1).astype(np.float64)
+    line("4096^2 TAN-SIP3 bicubic (config 1)", n1,
+         timed(src, tgt, img, X, Y, "bicubic", "poly"), "1M random target pixels")
+    c = synth.config3()
+    Y, X = np.mgrid[0:2048, 0:2048].astype(np.float64)
+    line("2048^2 TAN-SIP3 bilinear, Newton inverse (config 3)", X.size,
+         timed(c["src"][0], c["tgt"], c["images"][0], X.ravel(), Y.ravel(), "bilinear", "newton"),
+         "whole frame")
+    for name, cfg, ideg in (("64 frames -> 8192^2 bilinear (config 2)", synth.config2, 4),
+                            ("32 x 6000x4000 SIP5 -> 12000x8000 bicubic (config 4)",
+                             synth.config4, 6)):
+        c = cfg()
+        rng = synth.rng_for(8)
+        npx = 0
+        secs = 0.0
+        for f, img in zip(c["src"], c["images"]):
+            f = OW.with_inverse_sip(f, ideg)[0]
+            x0, y0, w, h = OR.target_bbox(f, c["tgt"])
+            k = max(1, (w * h) // 100)
+            X = (x0 + rng.integers(0, w, k)).astype(np.float64)
+            Y = (y0 + rng.integers(0, h, k)).astype(np.float64)
+            secs += timed(f, c["tgt"], img, X, Y, c["order"], "poly")
+            npx += k
+        line(name, npx, secs, "1 %% of every frame's bounding box (%d frames)" % len(c["src"]))
+        del c
+
+
 def run_extra(args):
     """Secondary measurements (not the bench line): the batch configuration (64 uneven frames
     onto 8192^2, one persistent graph launch vs 64 separate launches), the gradient configuration
@@ -615,14 +671,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sip3_4096",
                     choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "coadd32",
-                             "tsip4096", "lanczos4096", "bspline4096", "all"],
-                    help="sip3_4096: the bench line; the others print secondary measurements")
+                             "tsip4096", "lanczos4096", "bspline4096", "all", "oracle"],
+                    help="sip3_4096: the bench line; the others print secondary measurements "
+                         "(oracle: the CPU oracle on every configuration, no GPU)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "oracle":
+        if rank == 0:
+            run_oracle(args)
         return
     if args.workload != "sip3_4096":
         run_extra(args)
