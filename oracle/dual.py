@@ -228,6 +228,14 @@ def _interp_dual(img, x, y, order, valid, a=-0.5):
         t = c - i0  # Dual
         if order == _interp.BILINEAR:
             return i0.astype(np.int64), [1.0 - t, t]
+        if order == _interp.BSPLINE3:
+            # cubic B-spline at d = t + 1 - k, k = 0..3, as polynomials in t (s = 1 - t)
+            s = 1.0 - t
+            w0 = s * s * s * (1.0 / 6.0)
+            w1 = t * t * (0.5 * t - 1.0) + 2.0 / 3.0
+            w2 = s * s * (0.5 * s - 1.0) + 2.0 / 3.0
+            w3 = t * t * t * (1.0 / 6.0)
+            return (i0 - 1).astype(np.int64), [w0, w1, w2, w3]
         if order == _interp.LANCZOS3:
             # L(d) = sinc(d) sinc(d / 3) at d = t + 2 - k, k = 0..5, divided by their sum
             L = [sinc(t + float(2 - k)) * sinc((t + float(2 - k)) * (1.0 / 3.0))
@@ -247,6 +255,15 @@ def _interp_dual(img, x, y, order, valid, a=-0.5):
     yd = Dual(ys, np.where(ok, y.d, 0.0))
     ix, wx = weights(xd, xs)
     iy, wy = weights(yd, ys)
+    if order == _interp.BSPLINE3:
+        # img holds B-spline coefficients, continued by mirroring; footprint 1 where covered
+        num = Dual(np.zeros(n), np.zeros((k,) + n))
+        for j, wyj in enumerate(wy):
+            yy = _interp.mirror_index(iy + j, H)
+            for i, wxi in enumerate(wx):
+                xx = _interp.mirror_index(ix + i, W)
+                num = num + wxi * wyj * img[yy, xx].astype(np.float64)
+        return Dual(np.where(ok, num.v, 0.0), np.where(ok, num.d, 0.0))
     num = Dual(np.zeros(n), np.zeros((k,) + n))
     fp = Dual(np.zeros(n), np.zeros((k,) + n))
     for j, wyj in enumerate(wy):
@@ -267,7 +284,8 @@ def _interp_dual(img, x, y, order, valid, a=-0.5):
 def reproject_dual(src, tgt, img, xt, yt, order, inverse="newton"):
     """Dual-valued output of the reprojection at target pixels (xt, yt), with derivatives
     with respect to the source WCS parameters (param_names order)."""
-    order = {"nearest": 0, "bilinear": 1, "bicubic": 2, "lanczos3": 3}.get(order, order)
+    order = {"nearest": 0, "bilinear": 1, "bicubic": 2, "lanczos3": 3,
+             "bspline3": 4}.get(order, order)
     ra, dec = _wcs.pix2world(tgt, np.asarray(xt, np.float64), np.asarray(yt, np.float64))
     dsrc, names = dual_wcs(src)
     import oracle.dual as m

@@ -178,9 +178,25 @@ def interpolate(img, x, y, order, valid=None, a=-0.5, use_snap=True, nan_mask=Fa
     return val, fp
 
 
+def bspline3_prefilter_matrix(n):
+    """The 1-D prefilter as an n x n matrix: column j is the prefilter applied to unit vector
+    e_j (the map is linear, so this is the map itself)."""
+    return bspline3_prefilter_1d(np.eye(n), 0)
+
+
+def bspline3_prefilter_adjoint(g):
+    """Transpose of ``bspline3_prefilter``: the prefilter is C = My S Mx^T (rows by Mx, then
+    columns by My), so dL/dS = My^T (dL/dC) Mx."""
+    g = np.asarray(g, dtype=np.float64)
+    H, W = g.shape
+    return bspline3_prefilter_matrix(H).T @ g @ bspline3_prefilter_matrix(W)
+
+
 def interpolate_adjoint(img_shape, x, y, order, grad_val, valid=None, a=-0.5, use_snap=True):
     """Transpose of ``interpolate`` with respect to the source pixels: returns dL/dS given
-    dL/dval, i.e. dL/dS[j] = sum over (pixel, tap hitting j) of grad * w / footprint."""
+    dL/dval, i.e. dL/dS[j] = sum over (pixel, tap hitting j) of grad * w / footprint. For
+    bspline3 the source pixels are the B-spline coefficients (mirrored taps, footprint 1);
+    compose with ``bspline3_prefilter_adjoint`` for the image itself."""
     H, W = img_shape
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -191,6 +207,15 @@ def interpolate_adjoint(img_shape, x, y, order, grad_val, valid=None, a=-0.5, us
     ys = np.where(ok, y, 0.0)
     ix, wx = taps_1d(xs, order, a)
     iy, wy = taps_1d(ys, order, a)
+    if order == BSPLINE3:
+        g = np.where(ok, np.asarray(grad_val, dtype=np.float64), 0.0)
+        out = np.zeros((H, W))
+        for j in range(4):
+            yy = mirror_index(iy + j, H)
+            for i in range(4):
+                xx = mirror_index(ix + i, W)
+                np.add.at(out, (yy[ok], xx[ok]), (wx[i] * wy[j] * g)[ok])
+        return out
     fp = np.zeros(x.shape)
     for j in range(wy.shape[0]):
         for i in range(wx.shape[0]):

@@ -93,7 +93,16 @@ def test_dual_lanczos3_values_match_plain_oracle():
     np.testing.assert_allclose(o.v, val.ravel(), rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("order", ["bilinear", "bicubic", "lanczos3"])
+def test_dual_bspline3_values_match_plain_oracle():
+    """B-spline duals (the image is taken as the coefficient array) against the plain oracle."""
+    src, tgt, img, _ = _small_case("bspline3")
+    Y, X = np.mgrid[0:96, 0:96].astype(np.float64)
+    o, _ = D.reproject_dual(src, tgt, img, X.ravel(), Y.ravel(), "bspline3")
+    val, _, _, _ = R.reproject(src, tgt, img, "bspline3", inverse="newton", use_snap=False)
+    np.testing.assert_allclose(o.v, val.ravel(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", ["bilinear", "bicubic", "lanczos3", "bspline3"])
 def test_loss_gradient_matches_central_fd(order):
     src, tgt, img, ref = _small_case(order)
     loss, grad, names = D.loss_grad(src, tgt, img, ref, order)

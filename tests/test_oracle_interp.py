@@ -125,7 +125,7 @@ def test_matches_scipy_map_coordinates(order):
     np.testing.assert_allclose(fp[inner], 1.0, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC, I.LANCZOS3])
+@pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC, I.LANCZOS3, I.BSPLINE3])
 def test_adjoint_dot_product_and_dense(order):
     """<W s, g> = <s, W^T g> to 1e-12, and W built column by column from unit images equals the
     transpose built by the adjoint from unit gradients (brute force, 16x16)."""
@@ -149,6 +149,32 @@ def test_adjoint_dot_product_and_dense(order):
         e[p] = 1.0
         Wt[:, p] = I.interpolate_adjoint((H, Wd), x, y, order, e).ravel()
     np.testing.assert_allclose(Wm.T, Wt, rtol=0, atol=1e-14)
+
+
+def test_bspline3_image_adjoint_dense():
+    """The B-spline path from the image: value = evaluate(prefilter(S)). Its matrix, built
+    column by column from unit images, equals the transpose of prefilter_adjoint o
+    interpolate_adjoint built from unit gradients (brute force, 10x13 image, 150 positions)."""
+    rng = synth.rng_for(37)
+    H, Wd = 10, 13
+    x = rng.uniform(-0.5, Wd - 0.5, 150)
+    y = rng.uniform(-0.5, H - 0.5, 150)
+    Wm = np.zeros((150, H * Wd))
+    for j in range(H * Wd):
+        e = np.zeros(H * Wd)
+        e[j] = 1.0
+        Wm[:, j] = I.interpolate(I.bspline3_prefilter(e.reshape(H, Wd)), x, y, I.BSPLINE3)[0]
+    Wt = np.zeros((H * Wd, 150))
+    for p in range(150):
+        e = np.zeros(150)
+        e[p] = 1.0
+        Wt[:, p] = I.bspline3_prefilter_adjoint(
+            I.interpolate_adjoint((H, Wd), x, y, I.BSPLINE3, e)).ravel()
+    np.testing.assert_allclose(Wm.T, Wt, rtol=0, atol=1e-13)
+    # the prefilter matrix is the filter itself: its product with a vector is the filter
+    v = rng.standard_normal(H)
+    np.testing.assert_allclose(I.bspline3_prefilter_matrix(H) @ v,
+                               I.bspline3_prefilter_1d(v, 0), rtol=0, atol=1e-14)
 
 
 def test_reprojection_identity_wcs_bit_exact():
