@@ -185,7 +185,9 @@ class OraclePool:
 
     def __init__(self):
         import multiprocessing as mp
-        self.cores = len(os.sched_getaffinity(0))
+        # every host core, up to 32 processes (each holds the 64 MB frame and ~0.3 GB of
+        # oracle temporaries)
+        self.cores = min(len(os.sched_getaffinity(0)), 32)
         ctx = mp.get_context("spawn")
         # one thread per worker process: the workers inherit these at spawn
         saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
