@@ -14,7 +14,7 @@ Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on 
 stream, with a 512 MB write between steps to flush the 129 MB L2 (the flush is outside the
 events); barrier + synchronize around the timed loop; max over ranks. The reference arm
 (--impl reference) times the FP64 CPU oracle on a bounded pixel sample of the same workload, on
-every host core (one spawned process per core).
+every host core (one spawned process per core, at most 32).
 """
 from __future__ import annotations
 
