@@ -16,6 +16,7 @@
 #include <climits>
 
 #include "dfr_adjoint.cuh"
+#include "dfr_tile.cuh"
 
 namespace dfr {
 
@@ -84,10 +85,17 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
       float xr = 0.f, yr = 0.f, U = 0.f, V = 0.f, u = 0.f, v = 0.f;
       if (inside) {
         if (split) {
+          // position from the column cubic of the forward kernels (same bits); the chain
+          // rule's intermediate offsets from the exact per-pixel evaluation
           const Anchor& a = sanc;
-          float geo[4];
-          const bool ok = split_coords<-1>(P, a, float(P.x0 + gx - ax), float(P.y0 + gy - ay),
-                                           xr, yr, geo);
+          HP Q;
+          load_hot(P, Q);
+          const float dxa = float(P.x0 + gx - ax);
+          const int row = P.y0 + gy - ay + kCellH / 2;
+          const ColCubic cc = column_cubic(P, Q, a, dxa);
+          const bool ok = pixel_coords(P, Q, a, cc, dxa, row, xr, yr);
+          float geo[4], xe, ye;
+          split_coords<-1>(P, a, dxa, float(row - kCellH / 2), xe, ye, geo);
           bx = a.bx;
           by = a.by;
           cov = ok && xr >= -0.5f - float(bx) && xr <= float(P.W) - 0.5f - float(bx) &&

@@ -1,12 +1,13 @@
 // Tile-staged adjoint of the split-precision reprojection (dfr_reproject_backward), sm_103a.
 //
-// Same work decomposition as the forward split kernel: kCellsPerCta 32x32 anchor cells per
-// CTA, one per warp, each cell as 4 tiles of 32x8 (lane = column). Per tile the source box is
+// Same work decomposition as the forward split kernel: kCellsPerCta 32x64 anchor cells per
+// CTA, one per warp, each cell as 8 tiles of 32x8 (lane = column); source positions from the
+// same column cubics as the forward kernels (bit for bit). Per tile the source box is
 // staged by TMA into the warp's shared buffer (the taps are read from it) and a second buffer
 // of the same shape collects the tile's dL/dS contributions with shared-memory atomics; the
 // buffer is then added to grad_src with one global atomic per non-zero element (instead of one
 // per tap and pixel). Per-pixel parameter terms accumulate per lane in registers over the
-// cell's 32 pixels, and are summed over the warp once per cell. CTAs stride over the cells
+// cell's 64 pixels, and are summed over the warp once per cell. CTAs stride over the cells
 // (grid sized for residency) so every CTA's partial covers a fixed set of cells: the parameter
 // gradients are deterministic.
 #include <climits>
@@ -17,11 +18,11 @@
 namespace dfr {
 
 template <int ORDER, int IDEG, int FD>
-__device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HotPlan<IDEG, false>& Q,
-                                              const BwdExtra& B, const ChainConst& K,
-                                              const Anchor& a, int ox, int oy, int lane,
-                                              const float* box, float* gbox, const TileBox& tb,
-                                              bool want_params, float* acc) {
+__device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, const BwdExtra& B,
+                                              const ChainConst& K, const Anchor& a,
+                                              const ColCubic& cc, int ox, int oy, int r0,
+                                              int lane, const float* box, float* gbox,
+                                              const TileBox& tb, bool want_params, float* acc) {
   using T = Taps<ORDER>;
   constexpr int NTERM = nterms(FD);
   const int gx = ox + lane;
@@ -29,15 +30,18 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HotPlan<ID
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
   const float dx0 = float(Q.x0 + gx - a.ax);
-  const float dy0 = float(Q.y0 + oy - a.ay);
   const int bw = Q.box_w, bh = Q.box_h;
   const int nrows = min(kTileH, Q.h - oy);
 #pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
     float x, y, geo[4];
-    const bool ok = split_coords_core<IDEG, false, FD>(P, nullptr, Q.identity, Q.tsip,
-                                                       Q.newton, a, dx0, dy0 + float(r), x, y,
-                                                       geo);
+    const bool ok = pixel_coords(P, Q, a, cc, dx0, r0 + r, x, y);
+    if (want_params) {
+      // the chain rule's intermediate offsets, from the exact per-pixel evaluation
+      float xe, ye;
+      split_coords_core<IDEG, false, FD>(P, nullptr, Q.identity, Q.tsip, Q.newton, a, dx0,
+                                         float(r0 + r - kCellH / 2), xe, ye, geo);
+    }
     const bool cov = !tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi;
     float gxs = 0.f, gys = 0.f;
     if (cov) {
@@ -181,8 +185,7 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HotPlan<ID
 }
 
 // Adds the warp's gradient box to grad_src (non-zero elements inside the image) and clears it.
-template <int IDEG>
-__device__ __forceinline__ void flush_gbox(const HotPlan<IDEG, false>& Q, const BwdExtra& B,
+__device__ __forceinline__ void flush_gbox(const HP& Q, const BwdExtra& B,
                                            const TileBox& tb, float* gbox, int lane) {
   const int bw = Q.box_w, bh = Q.box_h;
   for (int j = 0; j < bh; ++j) {
@@ -217,7 +220,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
   for (int i = lane; i < B.box_floats; i += 32) gbox[i] = 0.f;
   __syncwarp();
   uint32_t phase = 0;
-  HotPlan<IDEG, false> Q;
+  bool dead = false;  // a wait gave up: no more box loads from this warp
+  bool pending = false;  // a box load has not been waited for
+  HP Q;
   load_hot(P, Q);
   const ChainConst K = chain_const(P);
   const bool want_params = B.grad_params != nullptr && ORDER != DFR_NEAREST;
@@ -236,6 +241,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
       const int cell = c0 + warp;
       const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
       const Anchor a = s_anc[warp];
+      const ColCubic cc = column_cubic(P, Q, a, float(Q.x0 + cox + lane - a.ax));
+      Q.use_tma = P.use_tma != 0 && !dead;
       float acc[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[q] = 0.f;
@@ -243,15 +250,22 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
         const int oy = coy + k * kTileH;
         if (oy >= Q.h) break;
         // the source values are needed only for the parameter terms
-        TileBox tb = tile_box<ORDER, IDEG, false>(P, Q, a, cox, oy, lane, box, bar, false,
-                                                  want_params);
+        TileBox tb = tile_box<ORDER>(P, Q, a, cc, cox, oy, k * kTileH, kTileH, lane, box, bar,
+                                     false, want_params);
         if (tb.empty) continue;
         if (tb.use_box && want_params) {
-          if (!mbar_wait(bar, phase)) tb.use_box = false;  // timed out: global memory instead
-          phase ^= 1u;
+          pending = true;
+          if (mbar_wait(bar, phase)) {
+            phase ^= 1u;
+            pending = false;
+          } else {  // timed out: global memory instead, and no more box loads
+            tb.use_box = false;
+            dead = true;
+            Q.use_tma = false;
+          }
         }
-        bwd_tile_rows<ORDER, IDEG, FD>(P, Q, B, K, a, cox, oy, lane, box, gbox, tb, want_params,
-                                       acc);
+        bwd_tile_rows<ORDER, IDEG, FD>(P, Q, B, K, a, cc, cox, oy, k * kTileH, lane, box, gbox,
+                                       tb, want_params, acc);
         if (tb.use_box && B.grad_src) {
           __syncwarp();
           flush_gbox(Q, B, tb, gbox, lane);
@@ -268,6 +282,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
     }
     __syncthreads();  // the anchors are rewritten by the next unit
   }
+  // a copy still in flight into this warp's buffer must land before the CTA exits
+  if (pending) mbar_wait(bar, phase, false);
   if (B.partials) {
     for (int q = threadIdx.x; q < NP; q += kWarps * 32) {
       double sum = 0.0;

@@ -10,14 +10,9 @@
 namespace dfr {
 
 template <int ORDER>
-static const void* coadd_for_order(bool split, int ideg) {
+static const void* coadd_for_order(bool split) {
   if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, true>);
-  switch (ideg) {
-    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0, false, true>);
-    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4, false, true>);
-    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6, false, true>);
-    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9, false, true>);
-  }
+  return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, true, kDefaultTileH>);
 }
 
 // Single-frame accumulating kernel for a plan (frames of a co-add are launched one after
@@ -25,11 +20,11 @@ static const void* coadd_for_order(bool split, int ideg) {
 const void* coadd_kernel(const FwdPlan& p0) {
   const bool split = (p0.flags & DFR_SPLIT) != 0;
   switch (p0.order) {
-    case DFR_NEAREST: return coadd_for_order<DFR_NEAREST>(split, p0.isip_deg);
-    case DFR_BILINEAR: return coadd_for_order<DFR_BILINEAR>(split, p0.isip_deg);
-    case DFR_BICUBIC: return coadd_for_order<DFR_BICUBIC>(split, p0.isip_deg);
-    case DFR_LANCZOS3: return coadd_for_order<DFR_LANCZOS3>(split, p0.isip_deg);
-    default: return coadd_for_order<DFR_BSPLINE3>(split, p0.isip_deg);
+    case DFR_NEAREST: return coadd_for_order<DFR_NEAREST>(split);
+    case DFR_BILINEAR: return coadd_for_order<DFR_BILINEAR>(split);
+    case DFR_BICUBIC: return coadd_for_order<DFR_BICUBIC>(split);
+    case DFR_LANCZOS3: return coadd_for_order<DFR_LANCZOS3>(split);
+    default: return coadd_for_order<DFR_BSPLINE3>(split);
   }
 }
 

@@ -167,18 +167,24 @@ __device__ __forceinline__ int mirror_index(int i, int n) {
   return i < n ? i : p - i;
 }
 
-// Cubic B-spline weights at distances 1 + t, t, 1 - t, 2 - t: (1-t)^3/6, 2/3 - t^2 + t^3/2,
-// 2/3 - (1-t)^2 + (1-t)^3/2, t^3/6.
-template <typename T>
-__device__ __forceinline__ void bspline3_weights(T t, T* w) {
-  const T s = T(1) - t;
-  const T sixth = T(1) / T(6), two3 = T(2) / T(3);
-  const T s2 = s * s, t2 = t * t;
-  w[0] = s2 * (s * sixth);
-  w[1] = fma(t2, fma(T(0.5), t, T(-1)), two3);
-  w[2] = fma(s2, fma(T(0.5), s, T(-1)), two3);
-  w[3] = t2 * (t * sixth);
-}
+// ---------------------------------------------------------------- explicitly rounded helpers
+// One value (float, double) or a pair (float2: packed FP32x2, each half exactly the scalar
+// operation). Every step is a rounding the compiler may not fuse or reorder, so an expression
+// written with these gives the same bits in every kernel and for either operand width.
+__device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float v_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float v_splat(float a, float) { return a; }
+__device__ __forceinline__ double v_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double v_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double v_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double v_splat(float a, double) { return double(a); }
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 v_splat(float a, float2) { return make_float2(a, a); }
+template <typename V>
+__device__ __forceinline__ V v_c(float a) { return v_splat(a, V()); }
 
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
@@ -213,65 +219,58 @@ __device__ __forceinline__ void lanczos3_weights(T t, T* w) {
   for (int k = 0; k < 6; ++k) w[k] *= inv;
 }
 
-// t = x - floor(x) in [0, 1). Nearest is handled by the caller (index shift when t >= 1/2).
-template <int ORDER, typename T>
-__device__ __forceinline__ void weights(T t, T* w) {
+// Interpolation weights at fraction t = x - floor(x) in [0, 1) (nearest: the caller shifts the
+// index when t >= 1/2). V = float, double, or float2 (two independent fractions at once). The
+// operation sequence is the definition: every FP32 gather path (shared-memory box, global
+// memory, the packed two-pixel rows) evaluates it, so they agree bit for bit.
+//   bilinear: 1 - t, t
+//   bicubic (Keys cubic convolution, a = -0.5, taps at distances 1 + t, t, 1 - t, 2 - t):
+//     t (t (1 - t/2) - 1/2), t^2 (3t/2 - 5/2) + 1, t (t (2 - 3t/2) + 1/2), t^2 (t/2 - 1/2)
+//   cubic B-spline: (1-t)^3/6, 2/3 - t^2 + t^3/2, 2/3 - (1-t)^2 + (1-t)^3/2, t^3/6
+template <int ORDER, typename V>
+__device__ __forceinline__ void weights_v(V t, V* w) {
   if (ORDER == DFR_NEAREST) {
-    w[0] = T(1);
+    w[0] = v_c<V>(1.f);
   } else if (ORDER == DFR_BILINEAR) {
-    w[0] = T(1) - t;
+    w[0] = v_add(v_c<V>(1.f), v_mul(v_c<V>(-1.f), t));
     w[1] = t;
-  } else if (ORDER == DFR_LANCZOS3) {
-    lanczos3_weights<T>(t, w);
   } else if (ORDER == DFR_BSPLINE3) {
-    bspline3_weights<T>(t, w);
-  } else {
-    // Keys cubic convolution, a = -0.5, at distances 1+t, t, 1-t, 2-t
-    const T s = T(1) - t;
-    const T t2 = t * t, s2 = s * s;
-    w[0] = (T(-0.5) * t) * s2;
-    w[1] = fma(t2, fma(T(1.5), t, T(-2.5)), T(1));
-    w[2] = fma(s2, fma(T(1.5), s, T(-2.5)), T(1));
-    w[3] = (T(-0.5) * t2) * s;
+    const V s = v_add(v_c<V>(1.f), v_mul(v_c<V>(-1.f), t));
+    const V sixth = v_c<V>(1.f / 6.f), two3 = v_c<V>(2.f / 3.f);
+    const V half = v_c<V>(0.5f), mone = v_c<V>(-1.f);
+    const V s2 = v_mul(s, s), t2 = v_mul(t, t);
+    w[0] = v_mul(s2, v_mul(s, sixth));
+    w[1] = v_fma(t2, v_fma(half, t, mone), two3);
+    w[2] = v_fma(s2, v_fma(half, s, mone), two3);
+    w[3] = v_mul(t2, v_mul(t, sixth));
+  } else {  // bicubic
+    const V t2 = v_mul(t, t);
+    w[0] = v_mul(t, v_fma(v_fma(v_c<V>(-0.5f), t, v_c<V>(1.f)), t, v_c<V>(-0.5f)));
+    w[1] = v_fma(t2, v_fma(v_c<V>(1.5f), t, v_c<V>(-2.5f)), v_c<V>(1.f));
+    w[2] = v_mul(t, v_fma(v_fma(v_c<V>(-1.5f), t, v_c<V>(2.f)), t, v_c<V>(0.5f)));
+    w[3] = v_mul(t2, v_fma(v_c<V>(0.5f), t, v_c<V>(-0.5f)));
   }
 }
 
-// weights() for x and y at once in packed FP32x2 arithmetic: w[k] = (wx_k, wy_k), each half
-// the same operation sequence (and bits) as weights().
+template <int ORDER, typename T>
+__device__ __forceinline__ void weights(T t, T* w) {
+  if (ORDER == DFR_LANCZOS3)
+    lanczos3_weights<T>(t, w);
+  else
+    weights_v<ORDER, T>(t, w);
+}
+
+// weights() for x and y at once: w[k] = (wx_k, wy_k), each half the bits of weights().
 template <int ORDER>
 __device__ __forceinline__ void weights2(float2 t, float2* w) {
-  const float2 one = make_float2(1.f, 1.f);
-  const float2 nt = make_float2(-t.x, -t.y);
-  if (ORDER == DFR_NEAREST) {
-    w[0] = one;
-  } else if (ORDER == DFR_BILINEAR) {
-    w[0] = __fadd2_rn(one, nt);
-    w[1] = t;
-  } else if (ORDER == DFR_LANCZOS3) {
+  if (ORDER == DFR_LANCZOS3) {
     float wx[6], wy[6];
     lanczos3_weights<float>(t.x, wx);
     lanczos3_weights<float>(t.y, wy);
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] = make_float2(wx[k], wy[k]);
-  } else if (ORDER == DFR_BSPLINE3) {
-    // bspline3_weights for both axes in FP32x2 (each half the same operations, so the same bits)
-    const float2 s = __fadd2_rn(one, nt);
-    const float2 sixth = make_float2(1.f / 6.f, 1.f / 6.f), two3 = make_float2(2.f / 3.f, 2.f / 3.f);
-    const float2 half = make_float2(0.5f, 0.5f), mone = make_float2(-1.f, -1.f);
-    const float2 s2 = __fmul2_rn(s, s), t2 = __fmul2_rn(t, t);
-    w[0] = __fmul2_rn(s2, __fmul2_rn(s, sixth));
-    w[1] = __ffma2_rn(t2, __ffma2_rn(half, t, mone), two3);
-    w[2] = __ffma2_rn(s2, __ffma2_rn(half, s, mone), two3);
-    w[3] = __fmul2_rn(t2, __fmul2_rn(t, sixth));
   } else {
-    const float2 s = __fadd2_rn(one, nt);
-    const float2 t2 = __fmul2_rn(t, t), s2 = __fmul2_rn(s, s);
-    const float2 mh = make_float2(-0.5f, -0.5f), c15 = make_float2(1.5f, 1.5f);
-    const float2 c25 = make_float2(-2.5f, -2.5f);
-    w[0] = __fmul2_rn(__fmul2_rn(mh, t), s2);
-    w[1] = __ffma2_rn(t2, __ffma2_rn(c15, t, c25), one);
-    w[2] = __ffma2_rn(s2, __ffma2_rn(c15, s, c25), one);
-    w[3] = __fmul2_rn(__fmul2_rn(mh, t2), s);
+    weights_v<ORDER, float2>(t, w);
   }
 }
 
@@ -557,7 +556,8 @@ __device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, int ax, int ay,
   if (!finite || !(h[2].hi > 0.f)) a.h2 = -1.f;  // the whole cell is treated as uncovered
 }
 
-__device__ __forceinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
+// Not inlined: once per cell, compiled once per translation unit.
+static __device__ __noinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
   a.ax = ax;
   a.ay = ay;
   if (P.identity) {
@@ -767,11 +767,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; on give-up sets the device status and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after kWaitNs of the global timer (or 2^26 polls,
+// whichever comes first), then, when `flag`, sets the device status word; returns false.
+constexpr uint64_t kWaitNs = 500000000ull;  // 0.5 s: far beyond any copy's latency
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, bool flag = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-  atomicOr(&g_status, kStatusTimeout);
+    if (global_ns() - t0 > kWaitNs) break;
+  }
+  if (flag) atomicOr(&g_status, kStatusTimeout);
   return false;
 }
 

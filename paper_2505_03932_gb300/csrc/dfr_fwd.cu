@@ -5,7 +5,7 @@
 // shared memory by a 2-D TMA load (or gathered straight from global memory), the footprint
 // computed from the in-bounds weights, value and footprint stored coalesced.
 //
-// Work units: FP64 path, a 32x8 tile per CTA; split path, kCellsPerCta 32x32 anchor cells per
+// Work units: FP64 path, a 32x8 tile per CTA; split path, kCellsPerCta 32x64 anchor cells per
 // CTA (one per warp). A CTA takes one unit (grid launch) or loops over units taken from an
 // atomic counter (persistent batch launch); the per-pixel arithmetic depends only on the pixel
 // and its cell, so both launch forms give equal bits.
@@ -15,70 +15,71 @@
 
 namespace dfr {
 
-// Source positions exactly as the split kernels compute them (same anchors, same arithmetic),
-// for the coordinate output of dfr_reproject; one thread per target pixel.
-template <int IDEG>
-__global__ void __launch_bounds__(256) split_coords_kernel(const __grid_constant__ FwdPlan P) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= int64_t(P.w) * P.h) return;
-  const int gx = int(i % P.w), gy = int(i / P.w);
+// Source positions exactly as the split kernels compute them (same anchors, same column
+// cubics), for the coordinate output of dfr_reproject; one thread per column of a cell.
+__global__ void __launch_bounds__(128) split_coords_kernel(const __grid_constant__ FwdPlan P) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(P.cells_x) * P.cells_y * kCellW) return;
+  const int cell = int(t / kCellW), col = int(t % kCellW);
+  const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
+  const int gx = cox + col;
+  if (gx >= P.w) return;
   Anchor a;
-  make_anchor(P, cell_anchor_x(P, gx), cell_anchor_y(P, gy), a);
-  float x, y;
-  const bool ok = split_coords_core<IDEG, false>(P, nullptr, P.identity != 0, P.tsip_deg > 0,
-                                                 plan_newton(P), a, float(P.x0 + gx - a.ax),
-                                                 float(P.y0 + gy - a.ay), x, y);
-  double* c = P.coords + 2 * i;
-  c[0] = ok ? double(a.bx) + double(x) : __longlong_as_double(0x7ff8000000000000ll);
-  c[1] = ok ? double(a.by) + double(y) : __longlong_as_double(0x7ff8000000000000ll);
+  make_anchor(P, P.x0 + cox + kCellW / 2, P.y0 + coy + kCellH / 2, a);
+  HP Q;
+  load_hot(P, Q);
+  const float dx = float(P.x0 + gx - a.ax);
+  const ColCubic cc = column_cubic(P, Q, a, dx);
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (int r = 0; r < kCellH && coy + r < P.h; ++r) {
+    float x, y;
+    const bool ok = pixel_coords(P, Q, a, cc, dx, r, x, y);
+    double* c = P.coords + 2 * (int64_t(coy + r) * P.w + gx);
+    c[0] = ok ? double(a.bx) + double(x) : nan;
+    c[1] = ok ? double(a.by) + double(y) : nan;
+  }
 }
 
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s) {
-  const int64_t n = int64_t(p0.w) * p0.h;
-  const int grid = int((n + 255) / 256);
+  const int64_t n = int64_t(p0.cells_x) * p0.cells_y * kCellW;
+  const int grid = int((n + 127) / 128);
   FwdPlan p = p0;
   void* args[] = {&p};
-  const void* k;
-  switch (p0.isip_deg) {
-    case 0: k = reinterpret_cast<const void*>(&split_coords_kernel<0>); break;
-    case 4: k = reinterpret_cast<const void*>(&split_coords_kernel<4>); break;
-    case 6: k = reinterpret_cast<const void*>(&split_coords_kernel<6>); break;
-    default: k = reinterpret_cast<const void*>(&split_coords_kernel<9>); break;
-  }
-  return cudaLaunchKernel(k, dim3(grid), dim3(256), args, 0, s);
+  return cudaLaunchKernel(reinterpret_cast<const void*>(&split_coords_kernel), dim3(grid),
+                          dim3(128), args, 0, s);
 }
 
 // ------------------------------------------------------------------ dispatch
 int forward_threads_default() { return kFp64Threads; }
 
-template <int ORDER, bool BATCH>
-static const void* split_for(int ideg) {
-  switch (ideg) {
-    case 0: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 0, BATCH, false>);
-    case 4: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 4, BATCH, false>);
-    case 6: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 6, BATCH, false>);
-    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, 9, BATCH, false>);
+// Single-frame split kernel of a tile height (8, 16 or 32 rows).
+template <int ORDER>
+static const void* split_for(int th) {
+  switch (th) {
+    case 8: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 8>);
+    case 32: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 32>);
+    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 16>);
   }
 }
 
 template <int ORDER>
-static const void* kernel_for_order(bool split, bool batch, int ideg) {
+static const void* kernel_for_order(bool split, int th) {
   if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, false>);
-  return batch ? split_for<ORDER, true>(ideg) : split_for<ORDER, false>(ideg);
+  return split_for<ORDER>(th);
 }
 
-// The kernel instantiation for a launch: order, flags and the packed inverse-SIP degree are
-// uniform over a launch and taken from p0; batch launches read their plans from a table.
+// The kernel instantiation for a launch: order, flags and tile height are uniform over a
+// launch and taken from p0; batch launches read their plans from a table.
 static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
   if (p0.flags & kFlagAccumulate) return batch ? nullptr : coadd_kernel(p0);
   const bool split = (p0.flags & DFR_SPLIT) != 0;
-  if (split && !batch && p0.tsip_deg > 0) return tsip_kernel(p0);
+  if (split && batch) return forward_batch_kernel(p0.order, p0.th);
   switch (p0.order) {
-    case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, batch, p0.isip_deg);
-    case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, batch, p0.isip_deg);
-    case DFR_BICUBIC: return kernel_for_order<DFR_BICUBIC>(split, batch, p0.isip_deg);
-    case DFR_LANCZOS3: return kernel_for_order<DFR_LANCZOS3>(split, batch, p0.isip_deg);
-    default: return kernel_for_order<DFR_BSPLINE3>(split, batch, p0.isip_deg);
+    case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, p0.th);
+    case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, p0.th);
+    case DFR_BICUBIC: return kernel_for_order<DFR_BICUBIC>(split, p0.th);
+    case DFR_LANCZOS3: return kernel_for_order<DFR_LANCZOS3>(split, p0.th);
+    default: return kernel_for_order<DFR_BSPLINE3>(split, p0.th);
   }
 }
 

@@ -130,13 +130,12 @@ __device__ __forceinline__ void fp64_tile(const FwdPlan& P, int tile) {
 // Co-add launches: ask L2 for a tile's accumulator rows (value and weight sums) one tile ahead,
 // so the read-modify-write of put_pixel<true> does not wait on HBM. Addresses inside the
 // output box only.
-template <bool ACC, int IDEG, bool PAIRS>
-__device__ __forceinline__ void prefetch_sums(const HotPlan<IDEG, PAIRS>& Q, int ox, int oy,
-                                              int lane) {
+template <bool ACC>
+__device__ __forceinline__ void prefetch_sums(const HP& Q, int ox, int oy, int rows, int lane) {
   if (!ACC) return;
   const int gx = ox + lane;
   if (gx >= Q.w || oy >= Q.h) return;
-  const int nrows = min(kTileH, Q.h - oy);
+  const int nrows = min(rows, Q.h - oy);
   for (int r = 0; r < nrows; ++r) {
     const int64_t o = int64_t(oy + r) * Q.out_pitch + gx;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(Q.out + o));
@@ -145,16 +144,17 @@ __device__ __forceinline__ void prefetch_sums(const HotPlan<IDEG, PAIRS>& Q, int
 }
 
 // ------------------------------------------------------------------ split-precision tiles
-// One warp owns a 32x8 tile at a time: lane = column, 8 rows per lane. Per pixel the source
-// position comes in FP32 from the anchor of the pixel's 32x32 cell; per tile a TMA load
-// stages the source box covering the tile's taps in the warp's shared buffer.
+// A warp owns a 32 x 64 cell (lane = column); its rows are processed in tiles of TH rows, each
+// with its source box staged in the warp's shared buffer by one TMA load. Per pixel the source
+// position comes from the lane's column cubic (column_cubic).
 
 // Value and footprint of one pixel from its taps. S(k, q) reads tap (row k, column q) and must
 // return 0 outside the image. A pixel whose taps all lie inside the image has footprint
 // exactly 1 (the weights sum to 1) and value = sum w S; otherwise out-of-image weights are
 // zeroed, footprint = (sum wx)(sum wy) and value = sum w S / footprint. Every gather path
-// (shared-memory box, global memory, the fast tile path) runs the same operation sequence:
-// row_k = sum_q wx_q S_kq, then value = sum_k wy_k row_k, each a chain of FMAs in index order.
+// (shared-memory box, global memory, the packed two-pixel rows) runs the same operation
+// sequence: row_k = wx_0 S_k0 + wx_1 S_k1 + ... (a product, then FMAs in index order), then
+// value = wy_0 row_0 + wy_1 row_1 + ... the same way.
 template <int ORDER, bool INTERIOR, typename Tap>
 __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by, int W, int H,
                                                const Tap& S) {
@@ -185,9 +185,10 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
 #pragma unroll
       for (int q = 0; q < T::n; ++q) {
         const int xx = mirror_index(ix + q, W);
-        row = fmaf(w[q].x, S(xx - q, yy - k, k, q), row);
+        const float sv = S(xx - q, yy - k, k, q);
+        row = q == 0 ? __fmul_rn(w[q].x, sv) : fmaf(w[q].x, sv, row);
       }
-      num = fmaf(w[k].y, row, num);
+      num = k == 0 ? __fmul_rn(w[k].y, row) : fmaf(w[k].y, row, num);
     }
     return make_float2(num, 1.f);
   }
@@ -206,8 +207,11 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
   for (int k = 0; k < T::n; ++k) {
     float row = 0.f;
 #pragma unroll
-    for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, S(ix, iy, k, q), row);
-    num = fmaf(w[k].y, row, num);
+    for (int q = 0; q < T::n; ++q) {
+      const float sv = S(ix, iy, k, q);
+      row = q == 0 ? __fmul_rn(w[q].x, sv) : fmaf(w[q].x, sv, row);
+    }
+    num = k == 0 ? __fmul_rn(w[k].y, row) : fmaf(w[k].y, row, num);
   }
   if (interior) return make_float2(num, 1.f);
   const float f = sx * sy;
@@ -289,119 +293,118 @@ __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int6
   return interp_pixel<ORDER, false>(x, y, bx, by, W, H, S);
 }
 
-// Rows of one tile: per pixel the split coordinates, coverage, then the gather from the box
-// (fast when the tile is interior) or from global memory.
-// Fast rows: the tile lies inside the bounding box, its widened source extent inside the image
-// and inside the loaded box, and the plan has no Newton inverse, NaN mask or identity. No
-// per-pixel branch: taps are read from the box at clamped positions and the rare pixel whose
-// taps leave the box (the curvature margin was too small) is redone from global memory.
-template <int ORDER, int IDEG, bool PAIRS, bool ACC, bool TSIP>
-__device__ __forceinline__ void tile_rows_fast(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
-                                               const Anchor& a, int ox, int oy, int lane,
-                                               const float* box, const TileBox& tb) {
+// floor(v) for |v| < 2^22 from v + 1.5 * 2^23 rounded toward minus infinity: the sum lies in
+// [2^23, 2^24), where the floats are the integers, so it equals floor(v) + 1.5 * 2^23 exactly
+// and its bit pattern is kFloorMagicBits + floor(v).
+constexpr float kFloorMagic = 12582912.f;
+constexpr uint32_t kFloorMagicBits = 0x4B400000u;
+
+// Fast rows of a tile: TH full rows of 32 columns whose taps all lie in the loaded box and in
+// the image (footprint 1), positions from a valid column cubic. Two rows per step in packed
+// FP32x2 arithmetic (the pair = the same column in rows r and r + 1): positions, floors and
+// fractions, weights, and the tap sums, each half the exact operation sequence of the
+// per-pixel path (interp_pixel), so both give the same bits. The box pitch is the
+// compile-time kBoxW, so every tap is an immediate offset from one address per pixel.
+template <int ORDER, bool ACC, int TH>
+__device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, const ColCubic& cc,
+                                               int gx, int oy, int r0, const float* box,
+                                               const TileBox& tb) {
   using T = Taps<ORDER>;
-  const int gx = ox + lane;
-  const float dx = float(Q.x0 + gx - a.ax);
-  float dy = float(Q.y0 + oy - a.ay);
-  const int bw = Q.box_w;
-  // a pixel is taken here only if all its taps lie in the widened extent, which is inside the
-  // image (no masking, footprint 1) and inside the box
-  const unsigned uxmax = unsigned(tb.ew - T::n), uymax = unsigned(tb.eh - T::n);
-  const int ux0 = a.bx + T::lo - tb.ex0, uy0 = a.by + T::lo - tb.ey0;
-  const int sx0 = tb.ex0 - tb.bx0, sy0 = tb.ey0 - tb.by0;  // extent origin within the box
-  float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
-  float* pf = Q.fp ? Q.fp + int64_t(oy) * Q.out_pitch + gx : nullptr;
-  uint32_t bad = 0;
-  // measured: by 4 for the plain kernels (1.6 % over 2; full unrolling costs instruction
-  // fetch), by 2 for Lanczos-3 and target-SIP rows (more registers per row)
-  constexpr int kUnroll = (ORDER == DFR_LANCZOS3 || TSIP) ? 2 : 4;
-#pragma unroll kUnroll
-  for (int r = 0; r < kTileH; ++r) {
-    float x, y;
-    const bool ok = split_coords_core<IDEG, PAIRS, -1, TSIP>(P, Q.cab, false, TSIP, false, a, dx,
-                                                             dy, x, y);
-    const float flx = floorf(x), fly = floorf(y);
-    const float2 t = make_float2(x - flx, y - fly);
-    int ux = int(flx) + ux0, uy = int(fly) + uy0;
+  constexpr int n = T::n;
+  // box index of a pixel's first tap: (floor(y) + by + lo - by0) kBoxW + floor(x) + bx + lo -
+  // bx0, with the floors as bit patterns (modular arithmetic)
+  const uint32_t kofs =
+      uint32_t((a.by + T::lo - tb.by0) * kBoxW + (a.bx + T::lo - tb.bx0)) -
+      kFloorMagicBits * uint32_t(kBoxW + 1);
+  const float2 cx0 = v_c<float2>(cc.c[0].x), cx1 = v_c<float2>(cc.c[1].x);
+  const float2 cx2 = v_c<float2>(cc.c[2].x), cx3 = v_c<float2>(cc.c[3].x);
+  const float2 cy0 = v_c<float2>(cc.c[0].y), cy1 = v_c<float2>(cc.c[1].y);
+  const float2 cy2 = v_c<float2>(cc.c[2].y), cy3 = v_c<float2>(cc.c[3].y);
+  const float2 magic = v_c<float2>(kFloorMagic);
+  const int64_t pitch = Q.out_pitch;
+  float* po = Q.out + int64_t(oy) * pitch + gx;
+  float* pf = Q.fp ? Q.fp + int64_t(oy) * pitch + gx : nullptr;
+  float2 s = make_float2(float(r0) - kCellMid, float(r0 + 1) - kCellMid);
+#pragma unroll 2
+  for (int i = 0; i < TH / 2; ++i) {
+    const float2 X = v_fma(v_fma(v_fma(cx3, s, cx2), s, cx1), s, cx0);
+    const float2 Y = v_fma(v_fma(v_fma(cy3, s, cy2), s, cy1), s, cy0);
+    const float2 mx = __fadd2_rd(X, magic), my = __fadd2_rd(Y, magic);
+    const float2 tx = v_sub(X, v_sub(mx, magic)), ty = v_sub(Y, v_sub(my, magic));
+    uint32_t ia = __float_as_uint(my.x) * uint32_t(kBoxW) + __float_as_uint(mx.x) + kofs;
+    uint32_t ib = __float_as_uint(my.y) * uint32_t(kBoxW) + __float_as_uint(mx.y) + kofs;
+    float2 num;
     if (ORDER == DFR_NEAREST) {
-      ux += t.x >= 0.5f;
-      uy += t.y >= 0.5f;
-    }
-    const bool in_ext = ok && unsigned(ux) <= uxmax && unsigned(uy) <= uymax;
-    bad |= uint32_t(!in_ext) << r;
-    const float* b = box + ((in_ext ? uy : 0) + sy0) * bw + (in_ext ? ux : 0) + sx0;
-    float num;
-    if (ORDER == DFR_NEAREST) {
-      num = b[0];
+      ia += uint32_t(tx.x >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.x >= 0.5f);
+      ib += uint32_t(tx.y >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.y >= 0.5f);
+      num = make_float2(box[ia], box[ib]);
     } else {
-      float2 w[T::n];
-      weights2<ORDER>(t, w);
-      num = 0.f;
+      float2 wx[n], wy[n];
+      if (ORDER == DFR_LANCZOS3) {
+        float ax[6], bxw[6], ay[6], byw[6];
+        lanczos3_weights<float>(tx.x, ax);
+        lanczos3_weights<float>(tx.y, bxw);
+        lanczos3_weights<float>(ty.x, ay);
+        lanczos3_weights<float>(ty.y, byw);
 #pragma unroll
-      for (int k = 0; k < T::n; ++k) {
-        float row = 0.f;
+        for (int q = 0; q < n; ++q) {
+          wx[q] = make_float2(ax[q], bxw[q]);
+          wy[q] = make_float2(ay[q], byw[q]);
+        }
+      } else {
+        weights_v<ORDER, float2>(tx, wx);
+        weights_v<ORDER, float2>(ty, wy);
+      }
+      const float* ba = box + ia;
+      const float* bb = box + ib;
 #pragma unroll
-        for (int q = 0; q < T::n; ++q) row = fmaf(w[q].x, b[k * bw + q], row);
-        num = fmaf(w[k].y, row, num);
+      for (int k = 0; k < n; ++k) {
+        float2 row;
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+          const float2 sv = make_float2(ba[k * kBoxW + q], bb[k * kBoxW + q]);
+          row = q == 0 ? v_mul(wx[q], sv) : v_fma(wx[q], sv, row);
+        }
+        num = k == 0 ? v_mul(wy[k], row) : v_fma(wy[k], row, num);
       }
     }
     if (ACC) {
-      if (in_ext) put_pixel<true>(po + int64_t(r) * Q.out_pitch, pf + int64_t(r) * Q.out_pitch,
-                                  num, 1.f);
+      put_pixel<true>(po, pf, num.x, 1.f);
+      put_pixel<true>(po + pitch, pf + pitch, num.y, 1.f);
     } else {
-      put_pixel<false>(po + int64_t(r) * Q.out_pitch, pf ? pf + int64_t(r) * Q.out_pitch : nullptr,
-                       num, 1.f);
+      __stcs(po, num.x);
+      __stcs(po + pitch, num.y);
+      if (pf) {
+        __stcs(pf, 1.f);
+        __stcs(pf + pitch, 1.f);
+      }
     }
-    dy += 1.f;
-  }
-  if (__any_sync(0xffffffffu, bad != 0) && bad) {
-    // pixels outside the box: the general per-pixel path, from global memory
-    const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
-    const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
-    for (int r = 0; r < kTileH; ++r) {
-      if (!((bad >> r) & 1u)) continue;
-      float x, y;
-      const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, false, TSIP, false, a, dx,
-                                                     float(Q.y0 + oy - a.ay) + float(r), x, y);
-      float2 vf = make_float2(0.f, 0.f);
-      if (ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi)
-        vf = gather_global<ORDER>(P.img, P.pitch, Q.W, Q.H, x, y, a.bx, a.by);
-      put_pixel<ACC>(po + int64_t(r) * Q.out_pitch, pf ? pf + int64_t(r) * Q.out_pitch : nullptr,
-                     vf.x, vf.y);
-    }
+    po += 2 * pitch;
+    if (pf) pf += 2 * pitch;
+    s = v_add(s, make_float2(2.f, 2.f));
   }
 }
 
-// General rows: per pixel the split coordinates, coverage, then the gather from the box (when
-// its taps are in the box) or from global memory.
-template <int ORDER, int IDEG, bool PAIRS, bool ACC, bool TSIP>
-__device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, PAIRS>& Q,
-                                          const Anchor& a, int ox, int oy, int lane,
+// General rows of a tile (per pixel): position (column cubic or exact), coverage, then the
+// gather from the box when the pixel's taps are in it, else from global memory; masking,
+// image edges and B-spline mirroring as the plan needs.
+template <int ORDER, bool ACC>
+__device__ __forceinline__ void tile_rows(const FwdPlan& P, const HP& Q, const Anchor& a,
+                                          const ColCubic& cc, int gx, int oy, int r0, int nrows,
                                           const float* box, const TileBox& tb) {
   using T = Taps<ORDER>;
-  if (oy >= Q.h) return;
-  // (the fast rows of a TSIP instantiation serve plans with target SIP, the others plans
-  // without; the remaining plans take the general rows)
-  const bool plain = !Q.identity && !Q.newton && !Q.mask && Q.tsip == TSIP;
-  if (plain && tb.use_box && tb.interior && ox + kTileW <= Q.w && oy + kTileH <= Q.h) {
-    tile_rows_fast<ORDER, IDEG, PAIRS, ACC, TSIP>(P, Q, a, ox, oy, lane, box, tb);
-    return;
-  }
-  const int gx = ox + lane;
-  if (gx >= Q.w) return;
+  if (oy >= Q.h || gx >= Q.w) return;
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
   const float dx = float(Q.x0 + gx - a.ax);
-  const float dy0 = float(Q.y0 + oy - a.ay);
   const int bw = Q.box_w, bh = Q.box_h;
-  const int nrows = min(kTileH, Q.h - oy);
+  nrows = min(nrows, Q.h - oy);
   float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
   float* pf = Q.fp ? Q.fp + int64_t(oy) * Q.out_pitch + gx : nullptr;
 #pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
     float x, y;
-    const bool ok = split_coords_core<IDEG, PAIRS>(P, Q.cab, Q.identity, Q.tsip, Q.newton, a,
-                                                   dx, dy0 + float(r), x, y);
+    const bool ok = pixel_coords(P, Q, a, cc, dx, r0 + r, x, y);
     float2 vf = make_float2(0.f, 0.f);
     if (!tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
       const float flx = floorf(x), fly = floorf(y);
@@ -447,14 +450,9 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HotPlan<IDEG, 
 }
 
 // ------------------------------------------------------------------ kernels
-// CTAs (of kWarps warps) per SM the register budget targets: 6 (80 registers) for single-frame
-// launches, whose inverse-SIP coefficients are constant-bank operands; 4 (128) for batch
-// launches, which hold them in registers.
-// Accumulating (co-add) launches hold the read-modify-write operands as well, and target-SIP
-// launches the target polynomial: 5 (96 registers). Lanczos-3 (36 taps): 4 (128 registers).
-constexpr int split_min_blocks(bool batch, bool acc, bool tsip, int order) {
-  return (batch || order == DFR_LANCZOS3) ? 4 : ((acc || tsip) ? 5 : 6);
-}
+// CTAs (of kWarps warps) per SM the register budget targets: 4 (128 registers: the two-pixel
+// rows hold two pixels' taps, weights and column coefficients at once).
+constexpr int kSplitMinBlocks = 4;
 
 __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
   int lo = 0, hi = L.nframes - 1;
@@ -484,16 +482,20 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
   }
 }
 
-// BATCH: frame plans in global memory (persistent launch over a frame table), inverse-SIP
-// coefficients held in registers as FP32x2 pairs; otherwise one frame whose plan is the kernel
-// parameter, read as constant-bank operands by scalar FMAs (fewer registers).
+// BATCH: frame plans in global memory (persistent launch over a frame table, work units from
+// an atomic counter); otherwise one frame whose plan is the kernel parameter, one unit per CTA
+// (from L.unit_begin).
 //
-// Work unit: kCellsPerCta consecutive 32x32 anchor cells. Warp 0 computes their anchors
-// (one lane per cell), then each warp processes the 4 tiles of each of its kCellsPerWarp cells,
-// requesting the source box of the next tile before gathering the current one.
-template <int ORDER, int IDEG, bool BATCH, bool ACC, bool TSIP = false>
-__global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP, ORDER)) fwd_split_kernel(
+// Work unit: kCellsPerCta consecutive 32x64 anchor cells. Warp 0 computes their anchors (one
+// lane per cell); each warp then takes one cell: its lanes fit their column cubics, and the
+// cell's rows go by in tiles of TH rows, the next tile's source box requested (TMA, double
+// buffered) before the current one is gathered. After a bounded wait gives up, the warp
+// issues no more box loads and gathers from global memory; before exiting it waits (bounded)
+// for any copy still in flight into its buffers.
+template <int ORDER, bool BATCH, bool ACC, int TH>
+__global__ void __launch_bounds__(kWarps * 32, kSplitMinBlocks) fwd_split_kernel(
     const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
+  static_assert(kCellH % TH == 0 && TH % 2 == 0, "tile height must divide the cell");
   extern __shared__ __align__(128) float box_raw[];
   __shared__ Anchor s_anc[kCellsPerCta];
   __shared__ int32_t s_frame[kCellsPerCta];
@@ -510,12 +512,14 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
   }
-  uint32_t phase = 0;  // bit b: parity of the next wait on buffer b
+  uint32_t phase = 0;    // bit b: parity of the next wait on buffer b
+  uint32_t pending = 0;  // bit b: a copy into buffer b has not been waited for
+  bool dead = false;     // a wait gave up: no more copies from this warp
   constexpr bool batch = BATCH;
+  constexpr int NT = kCellH / TH;
   // cells; a single-frame launch may cover units [unit_begin, unit_begin + grid) only (bands)
   const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
   const int nunits = (total + kCellsPerCta - 1) / kCellsPerCta;
-  // grid launch: one unit per CTA (from unit_begin); persistent: units from a counter
   int unit = blockIdx.x + L.unit_begin;
   if (batch) {
     if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
@@ -538,54 +542,51 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP
       s_cell[lane] = cell;
     }
     __syncthreads();
-    // this warp's tiles: kTilesPerCell per cell, cells warp*kCellsPerWarp ...
-    const int j0 = warp * kCellsPerWarp;
-    const int ncw = max(0, min(kCellsPerWarp, nc - j0));
-    const int nt = ncw * kTilesPerCell;
-    if (nt > 0) {
-      TileBox cur;
-      {
-        const FwdPlan& P = batch ? L.plans[s_frame[j0]] : p0;
-        HotPlan<IDEG, BATCH> Q;
-        load_hot(P, Q);
-        const Anchor a = s_anc[j0];
-        const int cell = s_cell[j0];
-        cur = tile_box<ORDER, IDEG, BATCH, TSIP>(P, Q, a, (cell % P.cells_x) * kCellW,
-                                                 (cell / P.cells_x) * kCellH, lane, box, &bar[0],
-                                                 batch);
-        prefetch_sums<ACC>(Q, (cell % P.cells_x) * kCellW, (cell / P.cells_x) * kCellH, lane);
-      }
-      for (int t = 0; t < nt; ++t) {
+    if (warp < nc) {
+      const FwdPlan& P = batch ? L.plans[s_frame[warp]] : p0;
+      HP Q;
+      load_hot(P, Q);
+      Q.use_tma = Q.use_tma && !dead;
+      const Anchor a = s_anc[warp];
+      const int cell = s_cell[warp];
+      const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
+      const int gx = cox + lane;
+      const ColCubic cc = column_cubic(P, Q, a, float(Q.x0 + gx - a.ax));
+      // fast rows need every column's cubic, bowing well inside the box margin
+      const bool fast_cell =
+          !Q.mask && __all_sync(0xffffffffu, cc.valid && cubic_bow(cc, TH) <= 0.5f) &&
+          cox + kCellW <= Q.w;
+      TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy, 0, TH, lane, box, &bar[0], batch,
+                                    true, L.tx_extra);
+      if (cur.use_box) pending |= 1u;
+      prefetch_sums<ACC>(Q, cox, coy, TH, lane);
+      for (int t = 0; t < NT; ++t) {
         const int b = t & 1;
         TileBox nxt;
         nxt.use_box = false;
-        if (t + 1 < nt) {
-          const int jn = j0 + (t + 1) / kTilesPerCell, kn = (t + 1) % kTilesPerCell;
-          const FwdPlan& Pn = batch ? L.plans[s_frame[jn]] : p0;
-          HotPlan<IDEG, BATCH> Qn;
-          load_hot(Pn, Qn);
-          const Anchor an = s_anc[jn];
-          const int celln = s_cell[jn];
-          nxt = tile_box<ORDER, IDEG, BATCH, TSIP>(
-              Pn, Qn, an, (celln % Pn.cells_x) * kCellW,
-              (celln / Pn.cells_x) * kCellH + kn * kTileH, lane, box + (b ^ 1) * L.box_floats,
-              &bar[b ^ 1], batch);
-          prefetch_sums<ACC>(Qn, (celln % Pn.cells_x) * kCellW,
-                             (celln / Pn.cells_x) * kCellH + kn * kTileH, lane);
+        if (t + 1 < NT) {
+          nxt = tile_box<ORDER>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
+                                box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch, true,
+                                L.tx_extra);
+          if (nxt.use_box) pending |= 1u << (b ^ 1);
+          prefetch_sums<ACC>(Q, cox, coy + (t + 1) * TH, TH, lane);
         }
-        const int j = j0 + t / kTilesPerCell, k = t % kTilesPerCell;
-        const FwdPlan& P = batch ? L.plans[s_frame[j]] : p0;
-        HotPlan<IDEG, BATCH> Q;
-        load_hot(P, Q);
-        const Anchor a = s_anc[j];
-        const int cell = s_cell[j];
         if (cur.use_box) {
-          if (!mbar_wait(&bar[b], (phase >> b) & 1u)) cur.use_box = false;  // timed out
-          phase ^= 1u << b;
+          if (mbar_wait(&bar[b], (phase >> b) & 1u)) {
+            phase ^= 1u << b;
+            pending &= ~(1u << b);
+          } else {  // timed out: this buffer's phase is unknown, gather from global memory
+            cur.use_box = false;
+            dead = true;
+            Q.use_tma = false;
+          }
         }
-        tile_rows<ORDER, IDEG, BATCH, ACC, TSIP>(P, Q, a, (cell % P.cells_x) * kCellW,
-                                      (cell / P.cells_x) * kCellH + k * kTileH, lane,
-                                      box + b * L.box_floats, cur);
+        const int oy = coy + t * TH;
+        const float* bt = box + b * L.box_floats;
+        if (fast_cell && cur.use_box && cur.interior && oy + TH <= Q.h)
+          tile_rows_fast<ORDER, ACC, TH>(Q, a, cc, gx, oy, t * TH, bt, cur);
+        else
+          tile_rows<ORDER, ACC>(P, Q, a, cc, gx, oy, t * TH, TH, bt, cur);
         cur = nxt;
       }
     }
@@ -595,6 +596,10 @@ __global__ void __launch_bounds__(kWarps * 32, split_min_blocks(BATCH, ACC, TSIP
     __syncthreads();
     unit = s_unit;
   }
+  // copies this warp issued and never saw complete (after a wait gave up) must land before
+  // the CTA's shared memory is released
+  for (int b = 0; b < 2; ++b)
+    if ((pending >> b) & 1u) mbar_wait(&bar[b], (phase >> b) & 1u, false);
 }
 
 }  // namespace dfr

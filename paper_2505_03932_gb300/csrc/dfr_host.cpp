@@ -274,8 +274,8 @@ bool HostMap::map_pq(double p, double q, double, double, double& xs, double& ys)
 
 namespace {
 
-// Source-box size for the TMA staging of one 64x16 tile: the largest source extent of a tile,
-// estimated from the map's Jacobian on a grid over the bounding box, with a 10% margin.
+// Jacobian and curvature bounds of the map over the bounding box (sampled on a 17 x 17 grid),
+// kept in the plan for sizing the source boxes of any tile height (set_tile_height).
 void size_box(FwdPlan& P) {
   HostMap M{&P};
   const int ns = 17;
@@ -314,26 +314,60 @@ void size_box(FwdPlan& P) {
                                 (4 * hh * hh));
       }
     }
-  const double A = kTileW - 1, B = kTileH - 1;
-  const double dev = (kxx * A * A + 2 * kxy * A * B + kyy * B * B) / 8.0;
-  P.box_margin = 1 + int(std::ceil(4.0 * dev));
-  const int ext = (P.order == DFR_LANCZOS3) ? 6
-                  : (P.order == DFR_BICUBIC || P.order == DFR_BSPLINE3) ? 4 : 2;
-  const double sx = 1.1 * (jxx * (kTileW - 1) + jxy * (kTileH - 1)) + 1.0;
-  const double sy = 1.1 * (jyx * (kTileW - 1) + jyy * (kTileH - 1)) + 1.0;
-  int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
-  int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
-  bw = (bw + 3) & ~3;
-  P.box_w = bw;
-  P.box_h = bh;
+  P.jac[0] = float(jxx);
+  P.jac[1] = float(jxy);
+  P.jac[2] = float(jyx);
+  P.jac[3] = float(jyy);
+  P.curv[0] = float(kxx);
+  P.curv[1] = float(kxy);
+  P.curv[2] = float(kyy);
 }
 
 int smem_for_floats(int floats);
 
+}  // namespace
+
+// Source box and its tensor map for tiles of th rows (th = 8, 16 or 32): kBoxW columns (the
+// compile-time pitch of the split kernels) by the rows a tile's taps can reach, from the
+// plan's Jacobian bound with a 10 % margin, widened by the curvature margin (the largest bow of
+// a column between a tile's first and last rows, times 4, at least 1 px) and the taps. Without
+// a TMA-capable source, or when the box would not fit in kBoxW columns or leave room for two
+// CTAs per SM, box loads are off (the kernels gather from global memory).
+void set_tile_height(FwdPlan& P, int th) {
+  P.th = th;
+  P.use_tma = 0;
+  P.box_w = P.box_h = 0;
+  if (!P.tma_ok) return;
+  const double B = th - 1;
+  P.box_margin = 1 + int(std::ceil(4.0 * double(P.curv[2]) * B * B / 8.0));
+  const int ext = (P.order == DFR_LANCZOS3) ? 6
+                  : (P.order == DFR_BICUBIC || P.order == DFR_BSPLINE3) ? 4 : 2;
+  const double sx = 1.1 * (double(P.jac[0]) * (kCellW - 1) + double(P.jac[1]) * B) + 1.0;
+  const double sy = 1.1 * (double(P.jac[2]) * (kCellW - 1) + double(P.jac[3]) * B) + 1.0;
+  const int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
+  const int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
+  if (bw > kBoxW || bh > 256 || smem_for_floats(kBoxW * bh) > 110 * 1024) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return;
+  cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
+  cuuint64_t gstride[1] = {cuuint64_t(P.pitch) * 4};
+  cuuint32_t bdim[2] = {cuuint32_t(kBoxW), cuuint32_t(bh)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&P.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.img), gdim,
+                   gstride, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return;
+  P.box_w = kBoxW;
+  P.box_h = bh;
+  P.use_tma = 1;
+}
+
+namespace {
+
 int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
                float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
                int32_t h, int32_t order, uint32_t flags, double* coords, int ideg_override,
-               FwdPlan& P) {
+               FwdPlan& P, int th = kDefaultTileH) {
   int rc;
   if ((rc = check_wcs(src, "source")) != DFR_OK) return rc;
   if ((rc = check_wcs(tgt, "target")) != DFR_OK) return rc;
@@ -474,24 +508,13 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
 
   // TMA staging of the source tile (split path only)
   P.use_tma = 0;
+  P.tma_ok = 0;
+  P.th = th;
   if ((flags & DFR_SPLIT) && !(flags & DFR_NO_TMA) && w > 0 && h > 0) {
     size_box(P);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
-    const int floats = (P.box_w * P.box_h + 31) & ~31;
-    // several CTAs per SM must fit beside their static shared memory
-    const bool fits = P.box_w <= 256 && P.box_h <= 256 && smem_for_floats(floats) <= 64 * 1024;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-    if (aligned && fits && enc) {
-      cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
-      cuuint64_t gstride[1] = {cuuint64_t(pitch) * 4};
-      cuuint32_t bdim[2] = {cuuint32_t(P.box_w), cuuint32_t(P.box_h)};
-      cuuint32_t estr[2] = {1, 1};
-      CUresult r = enc(&P.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), gdim,
-                       gstride, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r == CUDA_SUCCESS) P.use_tma = 1;
-    }
+    P.tma_ok = aligned && get_encode() != nullptr;
+    set_tile_height(P, th);
   }
   return DFR_OK;
 }
@@ -506,10 +529,10 @@ int smem_for(const FwdPlan& P) { return smem_for_floats(box_floats(P)); }
 // ------------------------------------------------------------------------------ device ctx
 // Library-owned device memory and graphs for the batched path, per device.
 struct GraphKey {
-  int n, order, flags, ideg, grid, smem, nfp;
+  int n, order, flags, ideg, grid, smem, th;
   bool operator<(const GraphKey& o) const {
-    return std::tie(n, order, flags, ideg, grid, smem, nfp) <
-           std::tie(o.n, o.order, o.flags, o.ideg, o.grid, o.smem, o.nfp);
+    return std::tie(n, order, flags, ideg, grid, smem, th) <
+           std::tie(o.n, o.order, o.flags, o.ideg, o.grid, o.smem, o.th);
   }
 };
 
@@ -526,9 +549,10 @@ struct DeviceCtx {
   cudaEvent_t done = nullptr;   // recorded after each batched launch (host buffers reusable)
   bool pending = false;
   std::map<GraphKey, cudaGraphExec_t> graphs;
-  // batch configuration per (order, flags, degree, log2 n): (1, lanes, -) = graph of
-  // single-frame kernels in `lanes` parallel chains, (0, ctas/SM, tma) = persistent kernel
-  std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> tuned;
+  // batch configuration per (order, flags, degree, log2 n): (1, lanes, -, th) = graph of
+  // single-frame kernels in `lanes` parallel chains, (0, ctas/SM, tma, th) = persistent kernel;
+  // th = tile height of the split kernels
+  std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int, int>> tuned;
   // fan-out graphs, keyed by the (kernel, grid, smem) signature of their frames
   // (the source graph stays alive: node updates on the executable graph name its nodes)
   struct Fan {
@@ -590,7 +614,7 @@ struct PlanKey {
   int32_t x0, y0, w, h, order;
   uint32_t flags;
   double* coords;
-  int32_t device, ideg;
+  int32_t device, ideg, th;
 };
 
 struct PlanEntry {
@@ -620,9 +644,10 @@ uint64_t key_hash(const PlanKey& k) {
 
 int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t pitch,
                 float* out, float* fp, int64_t out_pitch, int32_t x0, int32_t y0, int32_t w,
-                int32_t h, int32_t order, uint32_t flags, double* coords, int ideg, FwdPlan& P) {
+                int32_t h, int32_t order, uint32_t flags, double* coords, int ideg, FwdPlan& P,
+                int th = kDefaultTileH) {
   if (!src || !tgt) return build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h,
-                                      order, flags, coords, ideg, P);
+                                      order, flags, coords, ideg, P, th);
   PlanKey k;
   std::memset(&k, 0, sizeof(k));
   k.src = *src;
@@ -640,6 +665,7 @@ int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_
   k.flags = flags;
   k.coords = coords;
   k.ideg = ideg;
+  k.th = th;
   if (cudaGetDevice(&k.device) != cudaSuccess) k.device = -1;
   const uint64_t hk = key_hash(k);
   {
@@ -652,7 +678,7 @@ int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_
       }
   }
   int rc = build_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h, order, flags,
-                      coords, ideg, P);
+                      coords, ideg, P, th);
   if (rc != DFR_OK) return rc;
   std::lock_guard<std::mutex> lock(g_plan_mu);
   if (g_plans.size() >= kPlanCacheSize) {
@@ -668,6 +694,104 @@ int cached_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_
 }  // namespace dfr
 
 using namespace dfr;
+
+namespace {
+
+// Fault injection for the timeout test (DFR_FAULT_TX_EXTRA=<bytes>): single-frame split
+// launches add that many bytes to every box load's expected transaction count, so that the
+// bounded wait on it runs out while the copy itself completes. 0 unless the variable is set.
+uint32_t fault_tx_extra() {
+  static const uint32_t v = [] {
+    const char* e = std::getenv("DFR_FAULT_TX_EXTRA");
+    return e ? uint32_t(std::strtoul(e, nullptr, 10)) & 0xffff0u : 0u;
+  }();
+  return v;
+}
+
+// One single-frame launch of a plan (grid of work units, dynamic shared memory for the boxes).
+cudaError_t launch_single(const FwdPlan& P, cudaStream_t s) {
+  FwdLaunch L{};
+  L.total_tiles = P.tiles_x * P.tiles_y;
+  L.box_floats = box_floats(P);
+  int grid = L.total_tiles;
+  FwdPlan Pk = P;
+  if (P.flags & DFR_SPLIT) {
+    // work units of kCellsPerCta anchor cells, one per CTA; the coordinate output is a
+    // separate kernel (same arithmetic)
+    L.total_tiles = P.cells_x * P.cells_y;
+    grid = (L.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
+    L.tx_extra = fault_tx_extra();
+    Pk.coords = nullptr;
+  }
+  return launch_forward(Pk, L, grid, forward_threads_default(), smem_for(P), s);
+}
+
+bool autotune_on() {
+  const char* e = std::getenv("DFR_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+// Tile height of single-frame split launches (the rows of target pixels per staged source box:
+// 8, 16 or 32), per (device, order, flags, inverse-SIP degree, log2 of the output pixels).
+// Frames of at least 2^22 output pixels tune it on their first call: the three heights are
+// timed on the caller's own arguments with CUDA events (each candidate writes the same output
+// bits); smaller frames, captured streams and DFR_AUTOTUNE=0 use kDefaultTileH.
+std::mutex g_th_mu;
+std::map<std::array<int, 5>, int> g_th;
+
+int single_tile_height(const dfr_wcs* src, const dfr_wcs* tgt, const float* img,
+                       int64_t pitch, float* out, float* fp, int64_t out_pitch, int32_t x0,
+                       int32_t y0, int32_t w, int32_t h, int32_t order, uint32_t flags,
+                       cudaStream_t s) {
+  if (!src || !tgt || w <= 0 || h <= 0) return kDefaultTileH;
+  const int64_t px = int64_t(w) * h;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return kDefaultTileH;
+  const int ideg = sip_round_degree(std::max(src->ap_order, src->bp_order));
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= px) ++lg;
+  const std::array<int, 5> key{dev, order, int(flags), ideg, lg};
+  {
+    std::lock_guard<std::mutex> lock(g_th_mu);
+    auto it = g_th.find(key);
+    if (it != g_th.end()) return it->second;
+  }
+  if (px < (int64_t(1) << 22) || !autotune_on()) return kDefaultTileH;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return kDefaultTileH;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return kDefaultTileH;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return kDefaultTileH;
+  }
+  int best_th = kDefaultTileH;
+  float best = 1e30f;
+  for (int th : {8, 16, 32}) {
+    FwdPlan P;
+    if (cached_plan(src, tgt, img, pitch, out, fp, out_pitch, x0, y0, w, h, order, flags,
+                    nullptr, -1, P, th) != DFR_OK)
+      break;
+    bool ok = launch_single(P, s) == cudaSuccess;  // warm-up
+    ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+    for (int r = 0; r < 3 && ok; ++r) ok = launch_single(P, s) == cudaSuccess;
+    ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      best_th = th;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lock(g_th_mu);
+  g_th[key] = best_th;
+  return best_th;
+}
+
+}  // namespace
 
 // ================================================================================== C ABI
 extern "C" {
@@ -974,28 +1098,20 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
                   int64_t src_pitch, float* out, float* footprint, int64_t out_pitch, int32_t x0,
                   int32_t y0, int32_t out_w, int32_t out_h, int32_t order, uint32_t flags,
                   double* coords_out, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int th = (flags & DFR_SPLIT) ? single_tile_height(src, tgt, src_img, src_pitch, out,
+                                                          footprint, out_pitch, x0, y0, out_w,
+                                                          out_h, order, flags, s)
+                                     : kDefaultTileH;
   FwdPlan P;
   int rc = cached_plan(src, tgt, src_img, src_pitch, out, footprint, out_pitch, x0, y0, out_w,
-                       out_h, order, flags, coords_out, -1, P);
+                       out_h, order, flags, coords_out, -1, P, th);
   if (rc != DFR_OK) return rc;
   if (out_w == 0 || out_h == 0) return DFR_OK;
-  FwdLaunch L{};
-  L.total_tiles = P.tiles_x * P.tiles_y;
-  L.box_floats = box_floats(P);
-  int grid = L.total_tiles;
-  if (flags & DFR_SPLIT) {
-    // work units of kCellsPerCta anchor cells, one per CTA
-    L.total_tiles = P.cells_x * P.cells_y;
-    grid = (L.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
-  }
-  // the split kernels leave the coordinate output to a separate kernel (same arithmetic)
-  FwdPlan Pk = P;
-  if (flags & DFR_SPLIT) Pk.coords = nullptr;
-  cudaError_t e = launch_forward(Pk, L, grid, forward_threads_default(), smem_for(P),
-                                 static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_single(P, s);
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject launch");
   if ((flags & DFR_SPLIT) && coords_out) {
-    e = launch_split_coords(P, static_cast<cudaStream_t>(stream));
+    e = launch_split_coords(P, s);
     if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject coordinate launch");
   }
   return DFR_OK;
@@ -1018,7 +1134,7 @@ int dfr_device_status(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   e = read_and_clear_status_coadd(&d, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
-  e = read_and_clear_status_tsip(&t, static_cast<cudaStream_t>(stream));
+  e = read_and_clear_status_batch(&t, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   const int32_t s = a | b | c | d | t;
   if (s & kStatusTimeout) return fail(DFR_ERR_TIMEOUT, "a bounded device wait gave up");
@@ -1179,59 +1295,72 @@ int launch_fan(DeviceCtx& c, int n, int lanes, cudaStream_t s) {
 }
 
 // Batch autotuner, timed on the caller's data (outputs are rewritten identically by every
-// candidate): graphs of single-frame kernels in 1, 2, 4 or up to 64 parallel chains, and the
-// persistent kernel with several CTAs per SM, with and without TMA staging. Returns the
-// configuration tuple kept in DeviceCtx::tuned.
-std::tuple<int, int, int> autotune(DeviceCtx& c, int n, int floats, int total, cudaStream_t s) {
+// candidate): for each tile height of the split kernels (8, 16, 32 rows per staged box), graphs
+// of single-frame kernels in 1, 2, 4 or up to 64 parallel chains, and the persistent kernel
+// with several CTAs per SM, with and without TMA staging. Returns the configuration tuple kept
+// in DeviceCtx::tuned: (graph of chains 1 / persistent 0, chains or CTAs per SM, TMA, tile
+// height).
+std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStream_t s) {
   const int threads = forward_threads_default();
-  const int smem = smem_for_floats(floats);
-  const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
-  std::vector<std::pair<int, int>> cand;
-  for (int k : {1, 2, 3, 4, 6, 8})
-    if (k <= maxb) cand.push_back({k, smem > 0 ? 1 : 0});
-  if (smem > 0) {
-    const int maxb0 = forward_max_blocks_per_sm(c.h_plans[0], threads, 0);
-    for (int k : {2, 4, 8})
-      if (k <= maxb0) cand.push_back({k, 0});
-  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   std::vector<FwdPlan> saved(c.h_plans, c.h_plans + n);
+  const bool split = (saved[0].flags & DFR_SPLIT) != 0;
   float best = 1e30f;
-  std::tuple<int, int, int> pick = std::make_tuple(1, 1, 1);
-  for (int lanes : {1, 2, 4, 64}) {
-    // graphs of single-frame kernels in `lanes` parallel chains
-    if (lanes > 1 && lanes / 2 >= n) break;
-    bool ok = true;
-    for (int rep = 0; rep < 3 && ok; ++rep) {
-      if (rep == 1) cudaEventRecord(e0, s);
-      ok = launch_fan(c, n, lanes, s) == DFR_OK;
+  std::tuple<int, int, int, int> pick = std::make_tuple(1, 1, 1, kDefaultTileH);
+  for (int th : {8, 16, 32}) {
+    if (!split && th != kDefaultTileH) continue;
+    int floats = 0;
+    for (int f = 0; f < n; ++f) {
+      c.h_plans[f] = saved[f];
+      if (split && saved[f].th != th) set_tile_height(c.h_plans[f], th);
+      floats = std::max(floats, box_floats(c.h_plans[f]));
     }
-    cudaEventRecord(e1, s);
-    float ms = 0.f;
-    if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
-        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
-      best = ms;
-      pick = std::make_tuple(1, lanes, 1);
+    const std::vector<FwdPlan> base(c.h_plans, c.h_plans + n);
+    const int smem = smem_for_floats(floats);
+    const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
+    std::vector<std::pair<int, int>> cand;
+    for (int k : {1, 2, 3, 4, 6, 8})
+      if (k <= maxb) cand.push_back({k, smem > 0 ? 1 : 0});
+    if (smem > 0 && th == kDefaultTileH) {
+      const int maxb0 = forward_max_blocks_per_sm(c.h_plans[0], threads, 0);
+      for (int k : {2, 4, 8})
+        if (k <= maxb0) cand.push_back({k, 0});
     }
-  }
-  for (auto cd : cand) {
-    for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = cd.second ? saved[f].use_tma : 0;
-    const int fl = cd.second ? floats : 0;
-    const int grid = std::max(1, std::min(total, c.sms * cd.first));
-    float ms = 0.f;
-    bool ok = true;
-    for (int rep = 0; rep < 3 && ok; ++rep) {
-      if (rep == 1) cudaEventRecord(e0, s);
-      ok = enqueue_batch(c, n, grid, fl, s) == cudaSuccess;
+    for (int lanes : {1, 2, 4, 64}) {
+      // graphs of single-frame kernels in `lanes` parallel chains
+      if (lanes > 1 && lanes / 2 >= n) break;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        ok = launch_fan(c, n, lanes, s) == DFR_OK;
+      }
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+        best = ms;
+        pick = std::make_tuple(1, lanes, 1, th);
+      }
     }
-    cudaEventRecord(e1, s);
-    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      pick = std::make_tuple(0, cd.first, cd.second);
+    for (auto cd : cand) {
+      for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = cd.second ? base[f].use_tma : 0;
+      const int fl = cd.second ? floats : 0;
+      const int grid = std::max(1, std::min(total, c.sms * cd.first));
+      float ms = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        ok = enqueue_batch(c, n, grid, fl, s) == cudaSuccess;
+      }
+      cudaEventRecord(e1, s);
+      if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        pick = std::make_tuple(0, cd.first, cd.second, th);
+      }
     }
   }
   std::copy(saved.begin(), saved.end(), c.h_plans);
@@ -1258,35 +1387,36 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   int ideg = 0;
   for (int f = 0; f < n; ++f)
     ideg = std::max(ideg, sip_round_degree(std::max(frames[f].wcs.ap_order, frames[f].wcs.bp_order)));
+  const auto tkey = std::make_tuple(order, int(flags), ideg, 31 - __builtin_clz(unsigned(n)));
+  auto it = c.tuned.find(tkey);
+  const bool tuned = it != c.tuned.end();
+  std::tuple<int, int, int, int> cfg =
+      tuned ? it->second : std::make_tuple(1, 1, 1, int(kDefaultTileH));
   int64_t total = 0;
-  int floats = 0;
   for (int f = 0; f < n; ++f) {
     const dfr_frame& fr = frames[f];
     rc = cached_plan(&fr.wcs, tgt, fr.img, fr.pitch, fr.out, fr.footprint, fr.out_pitch, fr.x0,
-                     fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, c.h_plans[f]);
+                     fr.y0, fr.w, fr.h, order, flags, nullptr, ideg, c.h_plans[f],
+                     std::get<3>(cfg));
     if (rc != DFR_OK) {
       g_err = "frame " + std::to_string(f) + ": " + g_err;
       return rc;
     }
     c.h_starts[f] = int32_t(total);
     if (fr.w > 0 && fr.h > 0) total += dfr::batch_units(c.h_plans[f]);
-    floats = std::max(floats, box_floats(c.h_plans[f]));
   }
   if (total >= (int64_t(1) << 31)) return fail(DFR_ERR_INVALID_ARG, "batch too large");
   c.h_starts[n] = int32_t(total);
   if (total == 0) return DFR_OK;
 
-  const auto tkey = std::make_tuple(order, int(flags), ideg, 31 - __builtin_clz(unsigned(n)));
-  auto it = c.tuned.find(tkey);
-  std::tuple<int, int, int> cfg;
-  if (it != c.tuned.end()) {
-    cfg = it->second;
-  } else if (autotune_enabled()) {
-    cfg = autotune(c, n, floats, int(total), s);
+  if (!tuned) {
+    if (autotune_enabled()) cfg = autotune(c, n, int(total), s);
     c.tuned[tkey] = cfg;
-  } else {
-    cfg = std::make_tuple(1, 1, 1);  // one chain of single-frame kernels
+    if (std::get<3>(cfg) != kDefaultTileH && (flags & DFR_SPLIT))
+      for (int f = 0; f < n; ++f) set_tile_height(c.h_plans[f], std::get<3>(cfg));
   }
+  int floats = 0;
+  for (int f = 0; f < n; ++f) floats = std::max(floats, box_floats(c.h_plans[f]));
   if (std::get<0>(cfg) == 1) {
     // kernel parameters are copied into the graph: nothing host-side to protect afterwards
     return launch_fan(c, n, std::get<1>(cfg), s);
@@ -1296,7 +1426,7 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
     floats = 0;
   }
   const int grid = std::max(1, std::min(int(total), c.sms * std::get<1>(cfg)));
-  GraphKey gk{n, order, int(flags), ideg, grid, floats, 0};
+  GraphKey gk{n, order, int(flags), ideg, grid, floats, std::get<3>(cfg)};
   auto g = c.graphs.find(gk);
   if (g == c.graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -1619,8 +1749,9 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   // split path stages source and gradient boxes by tile, as sized by the plan
   float* dummy = reinterpret_cast<float*>(uintptr_t(16));
   const uint32_t pflags = (flags & DFR_SPLIT) ? flags : (flags | DFR_NO_TMA);
+  // the staged adjoint walks tiles of kTileH rows: its boxes are sized for that height
   int rc = cached_plan(src, tgt, src_img, src_pitch, dummy, nullptr, out_w, x0, y0, out_w, out_h,
-                       order, pflags, nullptr, -1, P);
+                       order, pflags, nullptr, -1, P, kTileH);
   if (rc != DFR_OK) return rc;
   if (out_w > 0 && out_h > 0) {
     if (!grad_out) return fail(DFR_ERR_INVALID_ARG, "grad_out must be non-NULL");

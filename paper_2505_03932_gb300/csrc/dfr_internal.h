@@ -18,21 +18,30 @@ constexpr int kMaxCoef = (DFR_MAX_SIP + 1) * (DFR_MAX_SIP + 2) / 2;  // 55
 __host__ __device__ constexpr int poly_off(int p, int n) { return p * (n + 1) - p * (p - 1) / 2; }
 __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) / 2; }
 
-// Target tile: 32 x 8 pixels, relative to the bounding-box origin; a warp processes a tile at a
-// time (lane = column), with one TMA-staged source box per tile.
+// Target tile: 32 x 8 pixels, relative to the bounding-box origin (the FP64 kernel's work unit
+// and the adjoint's staged tile; lane = column).
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
-// Anchor cell of the split path: 32 x 32 pixels (four tiles stacked in y), one anchor (about
-// 48-bit double-float arithmetic; FP64 with a target SIP) at its centre. A CTA of kWarps warps
-// takes kCellsPerCta consecutive cells; their anchors are computed together, one per lane, then
-// each warp processes the tiles of kCellsPerWarp cells.
+// Anchor cell of the split path: 32 x 64 pixels, one anchor (about 48-bit double-float
+// arithmetic; FP64 with a target SIP) at pixel (16, 32) of the cell. Each lane of the warp that
+// owns a cell holds, for its column, a cubic in the row that interpolates the exact FP32 map at
+// four rows and is checked at a fifth (see column_cubic). A CTA of kWarps warps takes
+// kCellsPerCta consecutive cells (one per warp); their anchors are computed together, one per
+// lane of warp 0. The forward kernel stages the source in boxes of TH rows (a template
+// parameter, 8, 16 or 32: the tile height the autotuner picks).
 constexpr int kCellW = 32;
-constexpr int kCellH = 32;
+constexpr int kCellH = 64;
 constexpr int kTilesPerCell = kCellH / kTileH;
 constexpr int kWarps = 4;
 constexpr int kCellsPerCta = 4;
 constexpr int kCellsPerWarp = kCellsPerCta / kWarps;
+// Source-box row pitch of the split kernels, in floats: a multiple of 32, so that the 32 lanes
+// of a warp (consecutive target columns) reading a tap from two adjacent source rows fall in
+// distinct shared-memory banks. It is also the TMA box width.
+constexpr int kBoxW = 64;
+// Default tile height (box rows of target pixels) of the split forward kernel.
+constexpr int kDefaultTileH = 16;
 
 // Per-frame forward plan. Built on the host in FP64; read by every CTA of the launch.
 struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requires
@@ -52,6 +61,10 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   int32_t W, H;
   int32_t use_tma, box_w, box_h;
   int32_t box_margin;        // px added around a tile's corner extent (covers map curvature)
+  int32_t th;                // tile height (rows) the box and its tensor map are sized for
+  int32_t tma_ok;            // the source allows TMA (16-byte aligned base and pitch)
+  float jac[4];              // host bounds of |dx/dX|, |dx/dY|, |dy/dX|, |dy/dY| (box sizing)
+  float curv[3];             // host bounds of the map's second derivatives (xx, xy, yy)
   int32_t identity;          // source and target WCS are bitwise equal
   // target WCS
   double crpix_t[2];         // CRPIX - 1 (0-based reference pixel)
@@ -98,6 +111,8 @@ struct FwdLaunch {
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
   int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
   int32_t unit_begin;        // single-frame split launch: first work unit (a band of the box)
+  uint32_t tx_extra;         // fault injection for the timeout test: bytes added to every box
+                             // load's expected count, so that its wait runs out (0 normally)
 };
 
 // Backward launch arguments. The kernel accumulates parameter gradients in a padded layout
@@ -129,6 +144,7 @@ enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s);
 const void* forward_kernel(const FwdPlan& p0);
+const void* forward_batch_kernel(int order, int th);              // dfr_fwd_batch.cu
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s);
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
 int forward_threads_default();
@@ -136,7 +152,7 @@ cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd_tile(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_coadd(int32_t* out, cudaStream_t s);
-cudaError_t read_and_clear_status_tsip(int32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_status_batch(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
@@ -144,12 +160,14 @@ int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats);
 int backward_threads_for(const FwdPlan& p0, int fd);
 const void* backward_tile_kernel(int order, int ideg, int fd);  // dfr_bwd_tile.cu
 const void* coadd_kernel(const FwdPlan& p0);                      // dfr_coadd.cu
-const void* tsip_kernel(const FwdPlan& p0);                       // dfr_fwd_tsip.cu
 cudaError_t launch_bspline_prefilter(const float* img, int64_t pitch, int32_t w, int32_t h,
                                      float* coef, int64_t coef_pitch, cudaStream_t s);
 cudaError_t launch_coadd_normalize(const float* sum_vf, const float* sum_f, int64_t pitch,
                                    int32_t w, int32_t h, float min_weight, float* mean,
                                    int64_t mean_pitch, cudaStream_t s);
+
+// Box size and tensor map of a plan for tiles of th rows (dfr_host.cpp).
+void set_tile_height(FwdPlan& P, int th);
 
 // Plan-builder access for translation units other than dfr_host.cpp.
 int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint32_t flags,
