@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
   constexpr int NTERM = nterms(FD);
   constexpr int NP = 6 + 2 * NTERM;
   __shared__ double sacc[NW][NP];
-  __shared__ Anchor sanc;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < NW * NP; i += NT) sacc[i / NP][i % NP] = 0.0;
   const bool split = (P.flags & DFR_SPLIT) != 0;
@@ -70,32 +69,31 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ox = (tile % P.tiles_x) * kTileW, oy = (tile / P.tiles_x) * kTileH;
-    const int ax = cell_anchor_x(P, ox), ay = cell_anchor_y(P, oy);
-    if (split) {
-      if (tid == 0) make_anchor(P, ax, ay, sanc);
-      __syncthreads();
-    }
 #pragma unroll 1
     for (int k = 0; k < PPT; ++k) {
       const int i = tid + k * NT;
       const int gx = ox + (i % kTileW), gy = oy + (i / kTileW);
       const bool inside = gx < P.w && gy < P.h;
+      // split plans: the warp (one tile row, 32 columns of one cell) fits the cell, as the
+      // forward kernels do
+      Anchor a;
+      ColCubic cc;
+      HP Q;
+      if (split) {
+        load_hot(P, Q);
+        cc = cell_fit(P, Q, ox, gy - gy % kCellH, lane, a);
+      }
       bool cov = false;
       int bx = 0, by = 0;
       float xr = 0.f, yr = 0.f, U = 0.f, V = 0.f, u = 0.f, v = 0.f;
       if (inside) {
         if (split) {
-          // position from the column cubic of the forward kernels (same bits); the chain
-          // rule's intermediate offsets from the exact per-pixel evaluation
-          const Anchor& a = sanc;
-          HP Q;
-          load_hot(P, Q);
-          const float dxa = float(P.x0 + gx - ax);
-          const int row = P.y0 + gy - ay + kCellH / 2;
-          const ColCubic cc = column_cubic(P, Q, a, dxa);
-          const bool ok = pixel_coords(P, Q, a, cc, dxa, row, xr, yr);
+          // position from the cell fit of the forward kernels (same bits); the chain rule's
+          // intermediate offsets from the exact per-pixel evaluation
+          const int row = gy % kCellH;
+          const bool ok = pixel_coords(P, Q, a, cc, lane, row, xr, yr);
           float geo[4], xe, ye;
-          split_coords<-1>(P, a, dxa, float(row - kCellH / 2), xe, ye, geo);
+          split_coords<-1>(P, a, float(lane - kAnchorCol), float(row) - kCellMid, xe, ye, geo);
           bx = a.bx;
           by = a.by;
           cov = ok && xr >= -0.5f - float(bx) && xr <= float(P.W) - 0.5f - float(bx) &&
@@ -226,8 +224,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
           }
       }
     }
-    __syncthreads();  // the shared anchor is rewritten by the next tile
   }
+  __syncthreads();  // every warp's accumulators are final
   if (B.partials) {
     for (int q = tid; q < NP; q += NT) {
       double s = 0.0;
@@ -281,12 +279,12 @@ static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {
 }
 
 int backward_threads_for(const FwdPlan& p0, int fd) {
-  return staged(p0, fd) ? kWarps * 32 : kBwdThreads;
+  return staged(p0, fd) ? kBwdWarps * 32 : kBwdThreads;
 }
 
 // Dynamic shared memory: per warp a source box and a gradient box, plus alignment slack.
 int backward_smem_bytes(const FwdPlan& p0, int fd, int box_floats) {
-  return staged(p0, fd) ? kWarps * 2 * box_floats * 4 + 128 : 0;
+  return staged(p0, fd) ? kBwdWarps * 2 * box_floats * 4 + 128 : 0;
 }
 
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes) {

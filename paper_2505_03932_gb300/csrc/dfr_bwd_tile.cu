@@ -1,8 +1,8 @@
 // Tile-staged adjoint of the split-precision reprojection (dfr_reproject_backward), sm_103a.
 //
-// Same work decomposition as the forward split kernel: kCellsPerCta 32x64 anchor cells per
-// CTA, one per warp, each cell as 8 tiles of 32x8 (lane = column); source positions from the
-// same column cubics as the forward kernels (bit for bit). Per tile the source box is
+// Work decomposition: kBwdCellsPerCta 32x64 cells per CTA, one per warp, each cell as 8 tiles
+// of 32x8 (lane = column); source positions from the same cell fits as the forward kernels
+// (bit for bit). Per tile the source box is
 // staged by TMA into the warp's shared buffer (the taps are read from it) and a second buffer
 // of the same shape collects the tile's dL/dS contributions with shared-memory atomics; the
 // buffer is then added to grad_src with one global atomic per non-zero element (instead of one
@@ -29,18 +29,18 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, con
   if (gx >= Q.w) return;
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
-  const float dx0 = float(Q.x0 + gx - a.ax);
+  const float dx0 = float(lane - kAnchorCol);
   const int bw = Q.box_w, bh = Q.box_h;
   const int nrows = min(kTileH, Q.h - oy);
 #pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
     float x, y, geo[4];
-    const bool ok = pixel_coords(P, Q, a, cc, dx0, r0 + r, x, y);
+    const bool ok = pixel_coords(P, Q, a, cc, lane, r0 + r, x, y);
     if (want_params) {
       // the chain rule's intermediate offsets, from the exact per-pixel evaluation
       float xe, ye;
       split_coords_core<IDEG, false, FD>(P, nullptr, Q.identity, Q.tsip, Q.newton, a, dx0,
-                                         float(r0 + r - kCellH / 2), xe, ye, geo);
+                                         float(r0 + r) - kCellMid, xe, ye, geo);
     }
     const bool cov = !tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi;
     float gxs = 0.f, gys = 0.f;
@@ -202,14 +202,13 @@ __device__ __forceinline__ void flush_gbox(const HP& Q, const BwdExtra& B,
 }
 
 template <int ORDER, int IDEG, int FD>
-__global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_constant__ FwdPlan P,
+__global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __grid_constant__ FwdPlan P,
                                                                 const __grid_constant__ BwdExtra B) {
   constexpr int NTERM = nterms(FD);
   constexpr int NP = 6 + 2 * NTERM;
   extern __shared__ __align__(128) float bsm_raw[];
-  __shared__ Anchor s_anc[kCellsPerCta];
-  __shared__ double s_acc[kWarps][NP];
-  __shared__ __align__(8) uint64_t s_bar[kWarps];
+  __shared__ double s_acc[kBwdWarps][NP];
+  __shared__ __align__(8) uint64_t s_bar[kBwdWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int skew = int((128u - (smem_addr(bsm_raw) & 127u)) & 127u) / 4;
   float* box = bsm_raw + skew + warp * 2 * B.box_floats;  // source box, then gradient box
@@ -227,21 +226,15 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
   const ChainConst K = chain_const(P);
   const bool want_params = B.grad_params != nullptr && ORDER != DFR_NEAREST;
   const int total = P.cells_x * P.cells_y;
-  const int nunits = (total + kCellsPerCta - 1) / kCellsPerCta;
+  const int nunits = (total + kBwdCellsPerCta - 1) / kBwdCellsPerCta;
   for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-    const int c0 = unit * kCellsPerCta;
-    const int nc = min(kCellsPerCta, total - c0);
-    if (warp == 0 && lane < nc) {
-      const int cell = c0 + lane;
-      make_anchor(P, P.x0 + (cell % P.cells_x) * kCellW + kCellW / 2,
-                  P.y0 + (cell / P.cells_x) * kCellH + kCellH / 2, s_anc[lane]);
-    }
-    __syncthreads();
+    const int c0 = unit * kBwdCellsPerCta;
+    const int nc = min(kBwdCellsPerCta, total - c0);
     if (warp < nc) {
       const int cell = c0 + warp;
       const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
-      const Anchor a = s_anc[warp];
-      const ColCubic cc = column_cubic(P, Q, a, float(Q.x0 + cox + lane - a.ax));
+      Anchor a;
+      const ColCubic cc = cell_fit(P, Q, cox, coy, lane, a);
       Q.use_tma = P.use_tma != 0 && !dead;
       float acc[NP];
 #pragma unroll
@@ -280,15 +273,15 @@ __global__ void __launch_bounds__(kWarps * 32, 4) bwd_split_kernel(const __grid_
         }
       }
     }
-    __syncthreads();  // the anchors are rewritten by the next unit
   }
   // a copy still in flight into this warp's buffer must land before the CTA exits
   if (pending) mbar_wait(bar, phase, false);
   if (B.partials) {
-    for (int q = threadIdx.x; q < NP; q += kWarps * 32) {
+    __syncthreads();  // every warp's accumulators are final
+    for (int q = threadIdx.x; q < NP; q += kBwdWarps * 32) {
       double sum = 0.0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) sum += s_acc[w][q];
+      for (int w = 0; w < kBwdWarps; ++w) sum += s_acc[w][q];
       B.partials[int64_t(blockIdx.x) * NP + q] = sum;
     }
   }

@@ -450,7 +450,6 @@ __device__ __forceinline__ bool source_from_target_fp64(const FwdPlan& P, double
 // into integer and fractional parts, and the FP32 coefficients of the local expansion.
 struct Anchor {
   int32_t bx, by;        // integer part of the anchor's source position
-  int32_t ax, ay;        // anchor target pixel (absolute)
   float f0x, f0y;        // anchor source position minus (bx, by)
   float U0, V0;          // anchor source intermediate offsets (for SIP evaluation)
   float a0, a1, b0, b1;  // numerators of the local homography
@@ -515,9 +514,9 @@ __device__ __forceinline__ FF ff_load(const float* hl) { return {hl[0], hl[1]}; 
 // this part and the anchor is a chain of dependent operations): the homography numerators
 // and denominator at the anchor, 1 / h2 by one Newton step from the FP32 reciprocal (24 -> 48
 // bits), the source position and its split into integer and fractional parts.
-__device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, int ax, int ay, Anchor& a) {
-  const FF u = ff_add(FF{float(ax), 0.f}, ff_neg(ff_load(P.crpix_t_ff[0])));
-  const FF v = ff_add(FF{float(ay), 0.f}, ff_neg(ff_load(P.crpix_t_ff[1])));
+__device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, float X, float Y, Anchor& a) {
+  const FF u = ff_add(FF{X, 0.f}, ff_neg(ff_load(P.crpix_t_ff[0])));
+  const FF v = ff_add(FF{Y, 0.f}, ff_neg(ff_load(P.crpix_t_ff[1])));
   a.tu = u.hi;
   a.tv = v.hi;
   a.tA = a.tB = 0.f;
@@ -556,17 +555,17 @@ __device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, int ax, int ay,
   if (!finite || !(h[2].hi > 0.f)) a.h2 = -1.f;  // the whole cell is treated as uncovered
 }
 
-// Not inlined: once per cell, compiled once per translation unit.
-static __device__ __noinline__ void make_anchor(const FwdPlan& P, int ax, int ay, Anchor& a) {
-  a.ax = ax;
-  a.ay = ay;
+// Anchor at target pixel position (X, Y) (absolute, exactly representable: integers or
+// quarter-integers). Not inlined: compiled once per translation unit.
+static __device__ __noinline__ void make_anchor(const FwdPlan& P, float X, float Y, Anchor& a) {
   if (P.identity) {
-    a.bx = ax;
-    a.by = ay;
-    a.f0x = a.f0y = 0.f;
+    a.bx = int32_t(floorf(X));
+    a.by = int32_t(floorf(Y));
+    a.f0x = __fsub_rn(X, floorf(X));
+    a.f0y = __fsub_rn(Y, floorf(Y));
     // true intermediate offsets of the anchor (used only by the adjoint's chain rule)
-    a.U0 = float(double(ax) - P.crpix_s[0]);
-    a.V0 = float(double(ay) - P.crpix_s[1]);
+    a.U0 = float(double(X) - P.crpix_s[0]);
+    a.V0 = float(double(Y) - P.crpix_s[1]);
     a.a0 = 1.f; a.a1 = 0.f; a.b0 = 0.f; a.b1 = 1.f;
     a.g20 = a.g21 = 0.f;
     a.h2 = 1.f;
@@ -574,13 +573,13 @@ static __device__ __noinline__ void make_anchor(const FwdPlan& P, int ax, int ay
     return;
   }
   if (P.tsip_deg <= 0) {
-    make_anchor_ff(P, ax, ay, a);
+    make_anchor_ff(P, X, Y, a);
     return;
   }
   // with target SIP: FP64 where absolute positions need it (the target SIP, the homography at
   // the anchor and the anchor's source position); the local expansion follows in FP32
-  const double u = __dsub_rn(double(ax), P.crpix_t[0]);
-  const double v = __dsub_rn(double(ay), P.crpix_t[1]);
+  const double u = __dsub_rn(double(X), P.crpix_t[0]);
+  const double v = __dsub_rn(double(Y), P.crpix_t[1]);
   double p = u, q = v;
   a.tu = float(u);
   a.tv = float(v);
@@ -626,16 +625,7 @@ static __device__ __noinline__ void make_anchor(const FwdPlan& P, int ax, int ay
   if (!finite || !(h2 > 0.0)) a.h2 = -1.f;  // the whole cell is treated as uncovered
 }
 
-// Anchor pixel (absolute target coordinates) of the 32x32 cell that holds bounding-box pixel
-// (gx, gy): the cell centre.
-__device__ __forceinline__ int cell_anchor_x(const FwdPlan& P, int gx) {
-  return P.x0 + (gx - gx % kCellW) + kCellW / 2;
-}
-__device__ __forceinline__ int cell_anchor_y(const FwdPlan& P, int gy) {
-  return P.y0 + (gy - gy % kCellH) + kCellH / 2;
-}
-
-// FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor pixel.
+// FP32 per-pixel part of the split path. (dx, dy): target pixel minus anchor position.
 // Writes the source position relative to (bx, by); returns false if undefined.
 // cab: the packed (AP, BP) coefficient pairs (IDEG > 0 with PAIRS: an unrolled FP32x2 Horner
 // of that degree over cab, which may live in registers; IDEG > 0 without PAIRS: the same in
@@ -651,8 +641,8 @@ __device__ __forceinline__ bool split_coords_core(const FwdPlan& P, const float2
                                                   const Anchor& a, float dx, float dy, float& xr,
                                                   float& yr, float* geo = nullptr) {
   if (identity) {
-    xr = dx;
-    yr = dy;
+    xr = __fadd_rn(a.f0x, dx);
+    yr = __fadd_rn(a.f0y, dy);
     if (geo) {
       geo[0] = geo[2] = dx;
       geo[1] = geo[3] = dy;

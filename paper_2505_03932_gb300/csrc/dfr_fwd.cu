@@ -5,8 +5,7 @@
 // shared memory by a 2-D TMA load (or gathered straight from global memory), the footprint
 // computed from the in-bounds weights, value and footprint stored coalesced.
 //
-// Work units: FP64 path, a 32x8 tile per CTA; split path, kCellsPerCta 32x64 anchor cells per
-// CTA (one per warp). A CTA takes one unit (grid launch) or loops over units taken from an
+// Work units: FP64 path, a 32x8 tile per CTA; split path, a 32x64 cell per one-warp CTA. A CTA takes one unit (grid launch) or loops over units taken from an
 // atomic counter (persistent batch launch); the per-pixel arithmetic depends only on the pixel
 // and its cell, so both launch forms give equal bits.
 #include <climits>
@@ -15,25 +14,21 @@
 
 namespace dfr {
 
-// Source positions exactly as the split kernels compute them (same anchors, same column
-// cubics), for the coordinate output of dfr_reproject; one thread per column of a cell.
-__global__ void __launch_bounds__(128) split_coords_kernel(const __grid_constant__ FwdPlan P) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= int64_t(P.cells_x) * P.cells_y * kCellW) return;
-  const int cell = int(t / kCellW), col = int(t % kCellW);
+// Source positions exactly as the split kernels compute them (same cell fits), for the
+// coordinate output of dfr_reproject; one warp per cell (lane = column).
+__global__ void __launch_bounds__(32) split_coords_kernel(const __grid_constant__ FwdPlan P) {
+  const int cell = blockIdx.x, lane = threadIdx.x & 31;
   const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
-  const int gx = cox + col;
-  if (gx >= P.w) return;
-  Anchor a;
-  make_anchor(P, P.x0 + cox + kCellW / 2, P.y0 + coy + kCellH / 2, a);
   HP Q;
   load_hot(P, Q);
-  const float dx = float(P.x0 + gx - a.ax);
-  const ColCubic cc = column_cubic(P, Q, a, dx);
+  Anchor a;
+  const ColCubic cc = cell_fit(P, Q, cox, coy, lane, a);
+  const int gx = cox + lane;
+  if (gx >= P.w) return;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   for (int r = 0; r < kCellH && coy + r < P.h; ++r) {
     float x, y;
-    const bool ok = pixel_coords(P, Q, a, cc, dx, r, x, y);
+    const bool ok = pixel_coords(P, Q, a, cc, lane, r, x, y);
     double* c = P.coords + 2 * (int64_t(coy + r) * P.w + gx);
     c[0] = ok ? double(a.bx) + double(x) : nan;
     c[1] = ok ? double(a.by) + double(y) : nan;
@@ -41,12 +36,10 @@ __global__ void __launch_bounds__(128) split_coords_kernel(const __grid_constant
 }
 
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s) {
-  const int64_t n = int64_t(p0.cells_x) * p0.cells_y * kCellW;
-  const int grid = int((n + 127) / 128);
   FwdPlan p = p0;
   void* args[] = {&p};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(&split_coords_kernel), dim3(grid),
-                          dim3(128), args, 0, s);
+  return cudaLaunchKernel(reinterpret_cast<const void*>(&split_coords_kernel),
+                          dim3(p0.cells_x * p0.cells_y), dim3(32), args, 0, s);
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -87,7 +80,7 @@ const void* forward_kernel(const FwdPlan& p0) { return forward_kernel_for(p0, fa
 
 // Block size of the kernel that serves this plan.
 static int block_threads(const FwdPlan& p0) {
-  return (p0.flags & DFR_SPLIT) ? kWarps * 32 : kFp64Threads;
+  return (p0.flags & DFR_SPLIT) ? kFwdWarps * 32 : kFp64Threads;
 }
 
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,

@@ -146,7 +146,7 @@ __device__ __forceinline__ void prefetch_sums(const HP& Q, int ox, int oy, int r
 // ------------------------------------------------------------------ split-precision tiles
 // A warp owns a 32 x 64 cell (lane = column); its rows are processed in tiles of TH rows, each
 // with its source box staged in the warp's shared buffer by one TMA load. Per pixel the source
-// position comes from the lane's column cubic (column_cubic).
+// position comes from the lane's column cubic (cell_fit).
 
 // Value and footprint of one pixel from its taps. S(k, q) reads tap (row k, column q) and must
 // return 0 outside the image. A pixel whose taps all lie inside the image has footprint
@@ -299,23 +299,39 @@ __device__ __noinline__ float2 gather_global(const float* __restrict__ img, int6
 constexpr float kFloorMagic = 12582912.f;
 constexpr uint32_t kFloorMagicBits = 0x4B400000u;
 
+// Shared-memory load at a 32-bit shared-window address. Not volatile: the compiler may schedule
+// these freely among the arithmetic; the caller derives every address from a token produced
+// after the barrier wait that made the box visible (box_token), so none can move above it.
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+  float v;
+  asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+
+// An opaque 0, ordered after the preceding volatile operations (the mbarrier wait).
+__device__ __forceinline__ uint32_t box_token() {
+  uint32_t z;
+  asm volatile("mov.u32 %0, 0;" : "=r"(z)::"memory");
+  return z;
+}
+
 // Fast rows of a tile: TH full rows of 32 columns whose taps all lie in the loaded box and in
 // the image (footprint 1), positions from a valid column cubic. Two rows per step in packed
 // FP32x2 arithmetic (the pair = the same column in rows r and r + 1): positions, floors and
 // fractions, weights, and the tap sums, each half the exact operation sequence of the
 // per-pixel path (interp_pixel), so both give the same bits. The box pitch is the
-// compile-time kBoxW, so every tap is an immediate offset from one address per pixel.
-template <int ORDER, bool ACC, int TH>
-__device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, const ColCubic& cc,
-                                               int gx, int oy, int r0, const float* box,
-                                               const TileBox& tb) {
+// compile-time kBoxW: a pixel's taps are immediate offsets from one shared address.
+template <int ORDER, bool ACC, int TH, bool FP>
+__device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a,
+                                                    const ColCubic& cc, int gx, int oy, int r0,
+                                                    uint32_t sbox, const TileBox& tb) {
   using T = Taps<ORDER>;
   constexpr int n = T::n;
-  // box index of a pixel's first tap: (floor(y) + by + lo - by0) kBoxW + floor(x) + bx + lo -
-  // bx0, with the floors as bit patterns (modular arithmetic)
-  const uint32_t kofs =
-      uint32_t((a.by + T::lo - tb.by0) * kBoxW + (a.bx + T::lo - tb.bx0)) -
-      kFloorMagicBits * uint32_t(kBoxW + 1);
+  // shared address of a pixel's first tap: sbox + 4 ((floor(y) + by + lo - by0) kBoxW +
+  // floor(x) + bx + lo - bx0), with the floors as bit patterns (modular arithmetic)
+  const uint32_t kb = sbox + 4u * (uint32_t((a.by + T::lo - tb.by0) * kBoxW +
+                                            (a.bx + T::lo - tb.bx0)) -
+                                   kFloorMagicBits * uint32_t(kBoxW + 1));
   const float2 cx0 = v_c<float2>(cc.c[0].x), cx1 = v_c<float2>(cc.c[1].x);
   const float2 cx2 = v_c<float2>(cc.c[2].x), cx3 = v_c<float2>(cc.c[3].x);
   const float2 cy0 = v_c<float2>(cc.c[0].y), cy1 = v_c<float2>(cc.c[1].y);
@@ -323,7 +339,7 @@ __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, con
   const float2 magic = v_c<float2>(kFloorMagic);
   const int64_t pitch = Q.out_pitch;
   float* po = Q.out + int64_t(oy) * pitch + gx;
-  float* pf = Q.fp ? Q.fp + int64_t(oy) * pitch + gx : nullptr;
+  float* pf = FP ? Q.fp + int64_t(oy) * pitch + gx : nullptr;
   float2 s = make_float2(float(r0) - kCellMid, float(r0 + 1) - kCellMid);
 #pragma unroll 2
   for (int i = 0; i < TH / 2; ++i) {
@@ -331,13 +347,13 @@ __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, con
     const float2 Y = v_fma(v_fma(v_fma(cy3, s, cy2), s, cy1), s, cy0);
     const float2 mx = __fadd2_rd(X, magic), my = __fadd2_rd(Y, magic);
     const float2 tx = v_sub(X, v_sub(mx, magic)), ty = v_sub(Y, v_sub(my, magic));
-    uint32_t ia = __float_as_uint(my.x) * uint32_t(kBoxW) + __float_as_uint(mx.x) + kofs;
-    uint32_t ib = __float_as_uint(my.y) * uint32_t(kBoxW) + __float_as_uint(mx.y) + kofs;
+    uint32_t ia = __float_as_uint(my.x) * uint32_t(4 * kBoxW) + __float_as_uint(mx.x) * 4u + kb;
+    uint32_t ib = __float_as_uint(my.y) * uint32_t(4 * kBoxW) + __float_as_uint(mx.y) * 4u + kb;
     float2 num;
     if (ORDER == DFR_NEAREST) {
-      ia += uint32_t(tx.x >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.x >= 0.5f);
-      ib += uint32_t(tx.y >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.y >= 0.5f);
-      num = make_float2(box[ia], box[ib]);
+      ia += 4u * (uint32_t(tx.x >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.x >= 0.5f));
+      ib += 4u * (uint32_t(tx.y >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.y >= 0.5f));
+      num = make_float2(lds_f32(ia), lds_f32(ib));
     } else {
       float2 wx[n], wy[n];
       if (ORDER == DFR_LANCZOS3) {
@@ -355,14 +371,13 @@ __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, con
         weights_v<ORDER, float2>(tx, wx);
         weights_v<ORDER, float2>(ty, wy);
       }
-      const float* ba = box + ia;
-      const float* bb = box + ib;
 #pragma unroll
       for (int k = 0; k < n; ++k) {
         float2 row;
 #pragma unroll
         for (int q = 0; q < n; ++q) {
-          const float2 sv = make_float2(ba[k * kBoxW + q], bb[k * kBoxW + q]);
+          const uint32_t off = uint32_t(4 * (k * kBoxW + q));
+          const float2 sv = make_float2(lds_f32(ia + off), lds_f32(ib + off));
           row = q == 0 ? v_mul(wx[q], sv) : v_fma(wx[q], sv, row);
         }
         num = k == 0 ? v_mul(wy[k], row) : v_fma(wy[k], row, num);
@@ -374,15 +389,25 @@ __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, con
     } else {
       __stcs(po, num.x);
       __stcs(po + pitch, num.y);
-      if (pf) {
+      if (FP) {
         __stcs(pf, 1.f);
         __stcs(pf + pitch, 1.f);
       }
     }
     po += 2 * pitch;
-    if (pf) pf += 2 * pitch;
+    if (FP) pf += 2 * pitch;
     s = v_add(s, make_float2(2.f, 2.f));
   }
+}
+
+template <int ORDER, bool ACC, int TH>
+__device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, const ColCubic& cc,
+                                               int gx, int oy, int r0, uint32_t sbox,
+                                               const TileBox& tb) {
+  if (ACC || Q.fp)
+    tile_rows_fast_impl<ORDER, ACC, TH, true>(Q, a, cc, gx, oy, r0, sbox, tb);
+  else
+    tile_rows_fast_impl<ORDER, ACC, TH, false>(Q, a, cc, gx, oy, r0, sbox, tb);
 }
 
 // General rows of a tile (per pixel): position (column cubic or exact), coverage, then the
@@ -396,7 +421,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HP& Q, const A
   if (oy >= Q.h || gx >= Q.w) return;
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
-  const float dx = float(Q.x0 + gx - a.ax);
+  const int lane = gx & (kCellW - 1);
   const int bw = Q.box_w, bh = Q.box_h;
   nrows = min(nrows, Q.h - oy);
   float* po = Q.out + int64_t(oy) * Q.out_pitch + gx;
@@ -404,7 +429,7 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HP& Q, const A
 #pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
     float x, y;
-    const bool ok = pixel_coords(P, Q, a, cc, dx, r0 + r, x, y);
+    const bool ok = pixel_coords(P, Q, a, cc, lane, r0 + r, x, y);
     float2 vf = make_float2(0.f, 0.f);
     if (!tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi) {
       const float flx = floorf(x), fly = floorf(y);
@@ -450,9 +475,9 @@ __device__ __forceinline__ void tile_rows(const FwdPlan& P, const HP& Q, const A
 }
 
 // ------------------------------------------------------------------ kernels
-// CTAs (of kWarps warps) per SM the register budget targets: 4 (128 registers: the two-pixel
+// Resident one-warp CTAs per SM the register budget targets: 16 (128 registers: the two-pixel
 // rows hold two pixels' taps, weights and column coefficients at once).
-constexpr int kSplitMinBlocks = 4;
+constexpr int kSplitMinBlocks = 16;
 
 __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
   int lo = 0, hi = L.nframes - 1;
@@ -482,119 +507,100 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
   }
 }
 
-// BATCH: frame plans in global memory (persistent launch over a frame table, work units from
-// an atomic counter); otherwise one frame whose plan is the kernel parameter, one unit per CTA
+// BATCH: frame plans in global memory (persistent launch over a frame table, cells taken from
+// an atomic counter); otherwise one frame whose plan is the kernel parameter, one cell per CTA
 // (from L.unit_begin).
 //
-// Work unit: kCellsPerCta consecutive 32x64 anchor cells. Warp 0 computes their anchors (one
-// lane per cell); each warp then takes one cell: its lanes fit their column cubics, and the
-// cell's rows go by in tiles of TH rows, the next tile's source box requested (TMA, double
-// buffered) before the current one is gathered. After a bounded wait gives up, the warp
-// issues no more box loads and gathers from global memory; before exiting it waits (bounded)
-// for any copy still in flight into its buffers.
+// A CTA is one warp and owns one 32 x 64 cell at a time: the warp fits the cell's column
+// cubics (cell_fit), then the cell's rows go by in tiles of TH rows, the next tile's source
+// box requested (TMA, double buffered) before the current one is gathered. After a bounded
+// wait gives up, the warp issues no more box loads and gathers from global memory; before
+// exiting it waits (bounded) for any copy still in flight into its buffers.
 template <int ORDER, bool BATCH, bool ACC, int TH>
-__global__ void __launch_bounds__(kWarps * 32, kSplitMinBlocks) fwd_split_kernel(
+__global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_kernel(
     const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
   static_assert(kCellH % TH == 0 && TH % 2 == 0, "tile height must divide the cell");
   extern __shared__ __align__(128) float box_raw[];
-  __shared__ Anchor s_anc[kCellsPerCta];
-  __shared__ int32_t s_frame[kCellsPerCta];
-  __shared__ int32_t s_cell[kCellsPerCta];
-  __shared__ __align__(8) uint64_t s_bar[kWarps][2];
-  __shared__ int32_t s_unit;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // 128-byte aligned source-box buffers (the launch reserves 128 bytes of slack); indexing the
-  // shared array itself keeps the compiler on shared-memory loads
+  __shared__ __align__(8) uint64_t s_bar[2];
+  const int lane = threadIdx.x & 31;
+  // 128-byte aligned source-box buffers (the launch reserves 128 bytes of slack)
   const int skew = int((128u - (smem_addr(box_raw) & 127u)) & 127u) / 4;
-  float* box = box_raw + skew + warp * 2 * L.box_floats;  // two buffers per warp
-  uint64_t* bar = &s_bar[warp][0];
+  float* box = box_raw + skew;  // two buffers of L.box_floats
+  uint64_t* bar = s_bar;
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
   }
+  __syncwarp();
   uint32_t phase = 0;    // bit b: parity of the next wait on buffer b
   uint32_t pending = 0;  // bit b: a copy into buffer b has not been waited for
   bool dead = false;     // a wait gave up: no more copies from this warp
   constexpr bool batch = BATCH;
   constexpr int NT = kCellH / TH;
-  // cells; a single-frame launch may cover units [unit_begin, unit_begin + grid) only (bands)
+  // cells; a single-frame launch may cover cells [unit_begin, unit_begin + grid) only (bands)
   const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
-  const int nunits = (total + kCellsPerCta - 1) / kCellsPerCta;
-  int unit = blockIdx.x + L.unit_begin;
+  int id = blockIdx.x + L.unit_begin;
   if (batch) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
-    __syncthreads();
-    unit = s_unit;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(L.counter, 1);
+    id = __shfl_sync(0xffffffffu, t, 0);
   }
-  while (unit < nunits) {
-    const int c0 = unit * kCellsPerCta;
-    const int nc = min(kCellsPerCta, total - c0);
-    if (warp == 0 && lane < nc) {  // anchors of the unit's cells, one per lane
-      int f = 0, cell = c0 + lane;
-      if (batch) {
-        f = frame_of(L, cell);
-        cell -= L.tile_start[f];
-      }
-      const FwdPlan& P = batch ? L.plans[f] : p0;
-      const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
-      make_anchor(P, P.x0 + cox + kCellW / 2, P.y0 + coy + kCellH / 2, s_anc[lane]);
-      s_frame[lane] = f;
-      s_cell[lane] = cell;
+  while (id < total) {
+    int f = 0, cell = id;
+    if (batch) {
+      f = frame_of(L, cell);
+      cell -= L.tile_start[f];
     }
-    __syncthreads();
-    if (warp < nc) {
-      const FwdPlan& P = batch ? L.plans[s_frame[warp]] : p0;
-      HP Q;
-      load_hot(P, Q);
-      Q.use_tma = Q.use_tma && !dead;
-      const Anchor a = s_anc[warp];
-      const int cell = s_cell[warp];
-      const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
-      const int gx = cox + lane;
-      const ColCubic cc = column_cubic(P, Q, a, float(Q.x0 + gx - a.ax));
-      // fast rows need every column's cubic, bowing well inside the box margin
-      const bool fast_cell =
-          !Q.mask && __all_sync(0xffffffffu, cc.valid && cubic_bow(cc, TH) <= 0.5f) &&
-          cox + kCellW <= Q.w;
-      TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy, 0, TH, lane, box, &bar[0], batch,
-                                    true, L.tx_extra);
-      if (cur.use_box) pending |= 1u;
-      prefetch_sums<ACC>(Q, cox, coy, TH, lane);
-      for (int t = 0; t < NT; ++t) {
-        const int b = t & 1;
-        TileBox nxt;
-        nxt.use_box = false;
-        if (t + 1 < NT) {
-          nxt = tile_box<ORDER>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
-                                box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch, true,
-                                L.tx_extra);
-          if (nxt.use_box) pending |= 1u << (b ^ 1);
-          prefetch_sums<ACC>(Q, cox, coy + (t + 1) * TH, TH, lane);
-        }
-        if (cur.use_box) {
-          if (mbar_wait(&bar[b], (phase >> b) & 1u)) {
-            phase ^= 1u << b;
-            pending &= ~(1u << b);
-          } else {  // timed out: this buffer's phase is unknown, gather from global memory
-            cur.use_box = false;
-            dead = true;
-            Q.use_tma = false;
-          }
-        }
-        const int oy = coy + t * TH;
-        const float* bt = box + b * L.box_floats;
-        if (fast_cell && cur.use_box && cur.interior && oy + TH <= Q.h)
-          tile_rows_fast<ORDER, ACC, TH>(Q, a, cc, gx, oy, t * TH, bt, cur);
-        else
-          tile_rows<ORDER, ACC>(P, Q, a, cc, gx, oy, t * TH, TH, bt, cur);
-        cur = nxt;
+    const FwdPlan& P = batch ? L.plans[f] : p0;
+    HP Q;
+    load_hot(P, Q);
+    Q.use_tma = Q.use_tma && !dead;
+    const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
+    const int gx = cox + lane;
+    Anchor a;
+    const ColCubic cc = cell_fit(P, Q, cox, coy, lane, a);
+    // fast rows need every column's cubic, bowing well inside the box margin
+    const bool fast_cell = !Q.mask && cc.valid &&
+                           __all_sync(0xffffffffu, cubic_bow(cc, TH) <= 0.5f) &&
+                           cox + kCellW <= Q.w;
+    TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy, 0, TH, lane, box, &bar[0], batch, true,
+                                  L.tx_extra);
+    if (cur.use_box) pending |= 1u;
+    prefetch_sums<ACC>(Q, cox, coy, TH, lane);
+    for (int t = 0; t < NT; ++t) {
+      const int b = t & 1;
+      TileBox nxt;
+      nxt.use_box = false;
+      if (t + 1 < NT) {
+        nxt = tile_box<ORDER>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
+                              box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch, true, L.tx_extra);
+        if (nxt.use_box) pending |= 1u << (b ^ 1);
+        prefetch_sums<ACC>(Q, cox, coy + (t + 1) * TH, TH, lane);
       }
+      uint32_t tok = 0;
+      if (cur.use_box) {
+        if (mbar_wait(&bar[b], (phase >> b) & 1u)) {
+          phase ^= 1u << b;
+          pending &= ~(1u << b);
+          tok = box_token();
+        } else {  // timed out: this buffer's phase is unknown, gather from global memory
+          cur.use_box = false;
+          dead = true;
+          Q.use_tma = false;
+        }
+      }
+      const int oy = coy + t * TH;
+      const float* bt = box + b * L.box_floats;
+      if (fast_cell && cur.use_box && cur.interior && oy + TH <= Q.h)
+        tile_rows_fast<ORDER, ACC, TH>(Q, a, cc, gx, oy, t * TH, smem_addr(bt) + tok, cur);
+      else
+        tile_rows<ORDER, ACC>(P, Q, a, cc, gx, oy, t * TH, TH, bt, cur);
+      cur = nxt;
     }
     if (!batch) break;
-    __syncthreads();  // every warp is done with this unit's anchors
-    if (threadIdx.x == 0) s_unit = atomicAdd(L.counter, 1);
-    __syncthreads();
-    unit = s_unit;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(L.counter, 1);
+    id = __shfl_sync(0xffffffffu, t, 0);
   }
   // copies this warp issued and never saw complete (after a wait gave up) must land before
   // the CTA's shared memory is released

@@ -329,8 +329,7 @@ int smem_for_floats(int floats);
 
 // Source box and its tensor map for tiles of th rows (th = 8, 16 or 32): kBoxW columns (the
 // compile-time pitch of the split kernels) by the rows a tile's taps can reach, from the
-// plan's Jacobian bound with a 10 % margin, widened by the curvature margin (the largest bow of
-// a column between a tile's first and last rows, times 4, at least 1 px) and the taps. Without
+// plan's Jacobian bound with a 3 % margin, widened by the curvature margin and the taps. Without
 // a TMA-capable source, or when the box would not fit in kBoxW columns or leave room for two
 // CTAs per SM, box loads are off (the kernels gather from global memory).
 void set_tile_height(FwdPlan& P, int th) {
@@ -339,11 +338,15 @@ void set_tile_height(FwdPlan& P, int th) {
   P.box_w = P.box_h = 0;
   if (!P.tma_ok) return;
   const double B = th - 1;
-  P.box_margin = 1 + int(std::ceil(4.0 * double(P.curv[2]) * B * B / 8.0));
+  // the kernels take every lane's first and last row exactly: the margin covers the bow of a
+  // column between them (twice the sampled bound), at least 1 px
+  P.box_margin = std::max(1, int(std::ceil(2.0 * double(P.curv[2]) * B * B / 8.0)));
   const int ext = (P.order == DFR_LANCZOS3) ? 6
                   : (P.order == DFR_BICUBIC || P.order == DFR_BSPLINE3) ? 4 : 2;
-  const double sx = 1.1 * (double(P.jac[0]) * (kCellW - 1) + double(P.jac[1]) * B) + 1.0;
-  const double sy = 1.1 * (double(P.jac[2]) * (kCellW - 1) + double(P.jac[3]) * B) + 1.0;
+  // (the Jacobian varies slowly; 3 % over its sampled maximum, and tiles whose taps still do
+  // not fit the box take the per-pixel path)
+  const double sx = 1.03 * (double(P.jac[0]) * (kCellW - 1) + double(P.jac[1]) * B) + 1.0;
+  const double sy = 1.03 * (double(P.jac[2]) * (kCellW - 1) + double(P.jac[3]) * B) + 1.0;
   const int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
   const int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
   if (bw > kBoxW || bh > 256 || smem_for_floats(kBoxW * bh) > 110 * 1024) return;
@@ -523,7 +526,7 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
 int box_floats(const FwdPlan& P) { return P.use_tma ? ((P.box_w * P.box_h + 31) & ~31) : 0; }
 
 // Dynamic shared memory of a split launch: two box buffers per warp plus 128 bytes of slack.
-int smem_for_floats(int floats) { return floats ? kWarps * 2 * floats * 4 + 128 : 0; }
+int smem_for_floats(int floats) { return floats ? kFwdWarps * 2 * floats * 4 + 128 : 0; }
 int smem_for(const FwdPlan& P) { return smem_for_floats(box_floats(P)); }
 
 // ------------------------------------------------------------------------------ device ctx
@@ -744,6 +747,14 @@ int single_tile_height(const dfr_wcs* src, const dfr_wcs* tgt, const float* img,
                        int32_t y0, int32_t w, int32_t h, int32_t order, uint32_t flags,
                        cudaStream_t s) {
   if (!src || !tgt || w <= 0 || h <= 0) return kDefaultTileH;
+  // DFR_TILE_H=8|16|32 pins the height (profiling one configuration under a profiler, whose
+  // serialised launches would mislead the tuner)
+  static const int pinned = [] {
+    const char* e = std::getenv("DFR_TILE_H");
+    const int v = e ? std::atoi(e) : 0;
+    return (v == 8 || v == 16 || v == 32) ? v : 0;
+  }();
+  if (pinned) return pinned;
   const int64_t px = int64_t(w) * h;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return kDefaultTileH;
@@ -1202,7 +1213,7 @@ int fan_items(const DeviceCtx& c, int n, std::vector<FanItem>& items) {
     if (P.flags & DFR_SPLIT) {
       it.launch.total_tiles = P.cells_x * P.cells_y;
       it.grid = (it.launch.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
-      it.threads = kWarps * 32;
+      it.threads = kFwdWarps * 32;
     } else {
       it.launch.total_tiles = P.tiles_x * P.tiles_y;
       it.grid = it.launch.total_tiles;
@@ -1320,12 +1331,14 @@ std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStre
     const std::vector<FwdPlan> base(c.h_plans, c.h_plans + n);
     const int smem = smem_for_floats(floats);
     const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
+    // CTAs per SM: one-warp CTAs for the split kernel, 256-thread CTAs for the FP64 kernel
+    const std::vector<int> ks = split ? std::vector<int>{6, 10, 16} : std::vector<int>{1, 2, 4, 8};
     std::vector<std::pair<int, int>> cand;
-    for (int k : {1, 2, 3, 4, 6, 8})
+    for (int k : ks)
       if (k <= maxb) cand.push_back({k, smem > 0 ? 1 : 0});
     if (smem > 0 && th == kDefaultTileH) {
       const int maxb0 = forward_max_blocks_per_sm(c.h_plans[0], threads, 0);
-      for (int k : {2, 4, 8})
+      for (int k : ks)
         if (k <= maxb0) cand.push_back({k, 0});
     }
     for (int lanes : {1, 2, 4, 64}) {
@@ -1802,7 +1815,7 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   const int smem = backward_smem_bytes(P, B.fd, B.box_floats);
   if (smem > 0) {
     // tile-staged kernel: CTAs resident at once stride over units of kCellsPerCta cells
-    const int units = (P.cells_x * P.cells_y + kCellsPerCta - 1) / kCellsPerCta;
+    const int units = (P.cells_x * P.cells_y + kBwdCellsPerCta - 1) / kBwdCellsPerCta;
     const int per_sm = backward_max_blocks_per_sm(P, B.fd, smem);
     B.grid = std::max(1, std::min(units, S.sms * per_sm));
   } else {

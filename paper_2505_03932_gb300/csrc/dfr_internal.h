@@ -23,19 +23,20 @@ __host__ __device__ constexpr int poly_ncoef(int n) { return (n + 1) * (n + 2) /
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
 constexpr int kTilePix = kTileW * kTileH;
-// Anchor cell of the split path: 32 x 64 pixels, one anchor (about 48-bit double-float
-// arithmetic; FP64 with a target SIP) at pixel (16, 32) of the cell. Each lane of the warp that
-// owns a cell holds, for its column, a cubic in the row that interpolates the exact FP32 map at
-// four rows and is checked at a fifth (see column_cubic). A CTA of kWarps warps takes
-// kCellsPerCta consecutive cells (one per warp); their anchors are computed together, one per
-// lane of warp 0. The forward kernel stages the source in boxes of TH rows (a template
-// parameter, 8, 16 or 32: the tile height the autotuner picks).
+// Cell of the split path: 32 x 64 pixels of the bounding box (cells tile it from its origin).
+// The warp that owns a cell samples the map at a 4 x 4 grid of nodes and four check points in
+// about 48-bit double-float arithmetic (FP64 with a target SIP), one point per lane, and each
+// lane interpolates the cubic in the row that gives its column's source positions (cell_fit).
+// The forward split kernel runs one warp (one cell) per CTA and stages the source in boxes of
+// TH rows (a template parameter, 8, 16 or 32: the tile height the autotuner picks). The staged
+// adjoint runs kBwdWarps warps per CTA, one cell each.
 constexpr int kCellW = 32;
 constexpr int kCellH = 64;
 constexpr int kTilesPerCell = kCellH / kTileH;
-constexpr int kWarps = 4;
-constexpr int kCellsPerCta = 4;
-constexpr int kCellsPerWarp = kCellsPerCta / kWarps;
+constexpr int kFwdWarps = 1;
+constexpr int kCellsPerCta = 1;
+constexpr int kBwdWarps = 4;
+constexpr int kBwdCellsPerCta = 4;
 // Source-box row pitch of the split kernels, in floats: a multiple of 32, so that the 32 lanes
 // of a warp (consecutive target columns) reading a tap from two adjacent source rows fall in
 // distinct shared-memory banks. It is also the TMA box width.

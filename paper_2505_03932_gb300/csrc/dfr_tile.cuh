@@ -75,64 +75,73 @@ static __device__ __noinline__ bool exact_coords(const FwdPlan& P, const HP& Q, 
   }
 }
 
-// ---------------------------------------------------------------- column cubic
-// Along one target column of a 32 x 64 cell the split map is a smooth function of the row. Each
-// lane evaluates it exactly (exact_coords) at the Chebyshev-Lobatto rows s = -a, -b, b, a of the
-// cell (s = row - 31.5, a = 31.5, b = 15.75) and takes the cubic through those four values:
-// with E = (f(s) + f(-s)) / 2 and O = (f(s) - f(-s)) / 2,
+// ---------------------------------------------------------------- cell fit
+// Cell coordinates: column c = 0..31 (the lane), row r = 0..63; sx = c - 15.5, s = r - 31.5
+// (exact). The cell's anchor sits at (sx, s) = (0.5, 0), i.e. target pixel
+// (x0 + cox + 16, y0 + coy + 31.5): the exact per-pixel evaluation of a cell pixel is
+// exact_coords(anchor, dx = c - 16, dy = s), relative to the anchor's integer base (bx, by).
+//
+// Along a column the map is a smooth function of s; across the cell, of sx. The warp samples it
+// exactly (make_anchor at the point, then exact_coords at offset 0: the double-float homography
+// and the FP32 inverse SIP) at the Chebyshev-Lobatto grid sx_i in {-A, -B, B, A} (A = 15.5,
+// B = 7.75) by s_j in {-a, -b, b, a} (a = 31.5, b = 15.75): lane i + 4 j takes node (i, j).
+// Each lane interpolates the four node rows at its own column, g_j = sum_i L_i(sx) f(i, j) (L
+// the Lagrange weights of the x nodes), and takes the cubic in s through g_0..g_3: with
+// E = (g(s) + g(-s)) / 2 and O = (g(s) - g(-s)) / 2,
 //   c2 = (E_a - E_b) / (a^2 - b^2),  c0 = E_b - c2 b^2,
 //   c3 = (O_a / a - O_b / b) / (a^2 - b^2),  c1 = O_b / b - c3 b^2.
-// A fifth exact value at s = 0, where the nodal polynomial (s^2 - a^2)(s^2 - b^2) has its
-// largest magnitude on the cell, must equal c0 within kCubicTol; otherwise (and for identity
-// maps, where positions must stay exact integers, and cells whose anchor or nodes are
-// undefined) the column falls back to the exact evaluation per pixel. Every kernel that needs
-// a split-path position (forward rows, coordinate output, adjoint) takes it from here, so all
-// agree bit for bit. A valid column has every pixel covered by the projection: the homography
-// denominator is linear along the column and positive at both end rows (the outer nodes).
+// Lanes 16-19 evaluate four check points exactly, at columns 16, 3, 28, 15 and s = 0, 24.875,
+// -24.875, -20, where the two nodal polynomials (s^2 - a^2)(s^2 - b^2) and (sx^2 - A^2)(sx^2 -
+// B^2) are at or near their largest; the first is the anchor. The cell's cubics are valid
+// when every point is defined and each check agrees with its column's cubic within kCubicTol;
+// otherwise (and for identity maps, whose positions must stay exact) every pixel of the cell
+// takes the exact evaluation. All split-path kernels take positions from here, so all agree
+// bit for bit. In a valid cell every pixel is covered by the projection: the homography
+// denominator is linear and positive at the four corner nodes.
+constexpr float kNodeXA = 15.5f, kNodeXB = 7.75f;
 constexpr float kNodeA = 31.5f, kNodeB = 15.75f;
 constexpr float kNodeB2 = 248.0625f;  // b^2, exact
 constexpr float kInvAB = 1.f / 744.1875f;  // 1 / (a^2 - b^2)
 constexpr float kInvA = 1.f / 31.5f, kInvB = 1.f / 15.75f;
 constexpr float kCubicTol = 1e-4f;  // px
-constexpr float kCellMid = 31.5f;   // s = row - kCellMid; dy = row - kCellH / 2
+constexpr float kCellMid = 31.5f;   // s = row - kCellMid
+constexpr int kAnchorCol = 16;      // dx = column - kAnchorCol
 
 struct ColCubic {
   float2 c[4];  // (x, y) polynomial coefficients in s, relative to the anchor's (bx, by)
-  bool valid;
+  bool valid;   // the same for the whole cell
 };
 
 __device__ __forceinline__ float2 v_sub(float2 a, float2 b) {
   return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
 
-static __device__ __noinline__ ColCubic column_cubic(const FwdPlan& P, const HP& Q, const Anchor& a,
-                                              float dx) {
-  float2 fam = make_float2(0.f, 0.f), fbm = fam, fbp = fam, fap = fam, f0 = fam;
-  bool ok = !Q.identity;
-#pragma unroll 1
-  for (int k = 0; k < 5; ++k) {
-    const float s = k == 0 ? -kNodeA : k == 1 ? -kNodeB : k == 2 ? kNodeB : k == 3 ? kNodeA : 0.f;
-    float x = 0.f, y = 0.f;
-    ok = exact_coords(P, Q, a, dx, __fsub_rn(s, 0.5f), x, y) && ok;
-    const float2 f = make_float2(x, y);
-    if (k == 0) fam = f;
-    if (k == 1) fbm = f;
-    if (k == 2) fbp = f;
-    if (k == 3) fap = f;
-    if (k == 4) f0 = f;
+// Lagrange weights of the x nodes at sx (exact products of quarter-integers, one rounding).
+__device__ __forceinline__ void lagrange_x(float sx, float L[4]) {
+  const float t[4] = {-kNodeXA, -kNodeXB, kNodeXB, kNodeXA};
+  // 1 / prod_{m != i} (t_i - t_m)
+  const float kInvDenX[4] = {-1.f / 5585.8125f, 1.f / 2792.90625f, -1.f / 2792.90625f,
+                             1.f / 5585.8125f};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float p = 1.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (m != i) p = __fmul_rn(p, __fsub_rn(sx, t[m]));
+    L[i] = __fmul_rn(p, kInvDenX[i]);
   }
+}
+
+// The cubic in s through the values g[j] at s = -a, -b, b, a.
+__device__ __forceinline__ void fit_s(const float2 g[4], float2 c[4]) {
   const float2 half = make_float2(0.5f, 0.5f);
-  const float2 Ea = v_mul(half, v_add(fap, fam)), Eb = v_mul(half, v_add(fbp, fbm));
-  const float2 Oa = v_mul(half, v_sub(fap, fam)), Ob = v_mul(half, v_sub(fbp, fbm));
-  ColCubic cc;
-  cc.c[2] = v_mul(v_sub(Ea, Eb), v_c<float2>(kInvAB));
-  cc.c[0] = v_fma(v_c<float2>(-kNodeB2), cc.c[2], Eb);
+  const float2 Ea = v_mul(half, v_add(g[3], g[0])), Eb = v_mul(half, v_add(g[2], g[1]));
+  const float2 Oa = v_mul(half, v_sub(g[3], g[0])), Ob = v_mul(half, v_sub(g[2], g[1]));
+  c[2] = v_mul(v_sub(Ea, Eb), v_c<float2>(kInvAB));
+  c[0] = v_fma(v_c<float2>(-kNodeB2), c[2], Eb);
   const float2 ra = v_mul(Oa, v_c<float2>(kInvA)), rb = v_mul(Ob, v_c<float2>(kInvB));
-  cc.c[3] = v_mul(v_sub(ra, rb), v_c<float2>(kInvAB));
-  cc.c[1] = v_fma(v_c<float2>(-kNodeB2), cc.c[3], rb);
-  // (NaN anywhere fails the comparisons)
-  cc.valid = ok && fabsf(cc.c[0].x - f0.x) <= kCubicTol && fabsf(cc.c[0].y - f0.y) <= kCubicTol;
-  return cc;
+  c[3] = v_mul(v_sub(ra, rb), v_c<float2>(kInvAB));
+  c[1] = v_fma(v_c<float2>(-kNodeB2), c[3], rb);
 }
 
 // Position of row s of a valid column: c0 + s (c1 + s (c2 + s c3)), both coordinates.
@@ -141,11 +150,103 @@ __device__ __forceinline__ float2 cubic_pos(const ColCubic& cc, float s) {
   return v_fma(v_fma(v_fma(cc.c[3], ss, cc.c[2]), ss, cc.c[1]), ss, cc.c[0]);
 }
 
-// Source position of row `row` (0..kCellH-1) of the cell column (dx from the anchor): the
-// column cubic where valid, else the exact evaluation (whose result says whether the pixel is
-// defined). Relative to (a.bx, a.by).
+// Cell-fit sample k (0-15 nodes, 16-19 checks) as (sx, s).
+__device__ __forceinline__ float2 cell_sample(int k) {
+  const float xs[4] = {-kNodeXA, -kNodeXB, kNodeXB, kNodeXA};
+  const float ss[4] = {-kNodeA, -kNodeB, kNodeB, kNodeA};
+  if (k < 16) return make_float2(xs[k & 3], ss[k >> 2]);
+  const float cxs[4] = {0.5f, -12.5f, 12.5f, -0.5f};  // columns 16, 3, 28, 15
+  const float css[4] = {0.f, 24.875f, -24.875f, -20.f};
+  return make_float2(cxs[k - 16], css[k - 16]);
+}
+
+// Exact source position at cell point (sx, s): the anchor there and its own offset-0 position
+// (relative to that anchor's base). Not inlined: once per lane and cell.
+static __device__ __noinline__ bool cell_point(const FwdPlan& P, const HP& Q, float X, float Y,
+                                               Anchor& an, float& x, float& y) {
+  make_anchor(P, X, Y, an);
+  return exact_coords(P, Q, an, 0.f, 0.f, x, y);
+}
+
+__device__ __forceinline__ Anchor shfl_anchor(const Anchor& a, int src) {
+  Anchor r;
+  r.bx = __shfl_sync(0xffffffffu, a.bx, src);
+  r.by = __shfl_sync(0xffffffffu, a.by, src);
+  r.f0x = __shfl_sync(0xffffffffu, a.f0x, src);
+  r.f0y = __shfl_sync(0xffffffffu, a.f0y, src);
+  r.U0 = __shfl_sync(0xffffffffu, a.U0, src);
+  r.V0 = __shfl_sync(0xffffffffu, a.V0, src);
+  r.a0 = __shfl_sync(0xffffffffu, a.a0, src);
+  r.a1 = __shfl_sync(0xffffffffu, a.a1, src);
+  r.b0 = __shfl_sync(0xffffffffu, a.b0, src);
+  r.b1 = __shfl_sync(0xffffffffu, a.b1, src);
+  r.g20 = __shfl_sync(0xffffffffu, a.g20, src);
+  r.g21 = __shfl_sync(0xffffffffu, a.g21, src);
+  r.h2 = __shfl_sync(0xffffffffu, a.h2, src);
+  r.tu = __shfl_sync(0xffffffffu, a.tu, src);
+  r.tv = __shfl_sync(0xffffffffu, a.tv, src);
+  r.tA = __shfl_sync(0xffffffffu, a.tA, src);
+  r.tB = __shfl_sync(0xffffffffu, a.tB, src);
+  return r;
+}
+
+// Warp-collective (all 32 lanes, lane = column): the cell's anchor and this lane's column
+// cubic. (cox, coy): the cell's first column and row in the bounding box.
+__device__ __forceinline__ ColCubic cell_fit(const FwdPlan& P, const HP& Q, int cox, int coy,
+                                             int lane, Anchor& anchor) {
+  const unsigned full = 0xffffffffu;
+  bool ok = true;
+  float x = 0.f, y = 0.f;
+  Anchor an;
+  if (lane < 20) {
+    const float2 p = cell_sample(lane);
+    const float X = float(Q.x0 + cox) + (p.x + 15.5f), Y = float(Q.y0 + coy) + (p.y + kCellMid);
+    ok = cell_point(P, Q, X, Y, an, x, y);
+  }
+  anchor = shfl_anchor(an, 16);
+  // sample positions relative to the anchor's base
+  if (lane < 20) {
+    const int ox = an.bx - anchor.bx, oy = an.by - anchor.by;
+    ok = ok && abs(ox) < (1 << 20) && abs(oy) < (1 << 20);
+    x = __fadd_rn(x, float(ox));
+    y = __fadd_rn(y, float(oy));
+    ok = ok && fabsf(x) < 1048576.f && fabsf(y) < 1048576.f;
+  }
+  ColCubic cc;
+  // this column's values at the four node rows
+  float L[4];
+  lagrange_x(float(lane) - 15.5f, L);
+  float2 g[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = make_float2(__shfl_sync(full, x, i + 4 * j), __shfl_sync(full, y, i + 4 * j));
+      const float2 Li = make_float2(L[i], L[i]);
+      g[j] = i == 0 ? v_mul(Li, f) : v_fma(Li, f, g[j]);
+    }
+  }
+  fit_s(g, cc.c);
+  // checks: lane 16 + k holds the exact value at column kc[k], row s_k
+  bool chk = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float ex = __shfl_sync(full, x, 16 + k), ey = __shfl_sync(full, y, 16 + k);
+    const float2 sk = cell_sample(16 + k);
+    if (lane == int(sk.x + 15.5f)) {
+      const float2 q = cubic_pos(cc, sk.y);
+      chk = fabsf(q.x - ex) <= kCubicTol && fabsf(q.y - ey) <= kCubicTol;
+    }
+  }
+  cc.valid = __all_sync(full, ok && chk) && !Q.identity;
+  return cc;
+}
+
+// Source position of row `row` (0..kCellH-1) of this lane's column: the column cubic where the
+// cell is valid, else the exact evaluation (whose result says whether the pixel is defined).
+// Relative to (anchor.bx, anchor.by).
 __device__ __forceinline__ bool pixel_coords(const FwdPlan& P, const HP& Q, const Anchor& a,
-                                             const ColCubic& cc, float dx, int row, float& x,
+                                             const ColCubic& cc, int lane, int row, float& x,
                                              float& y) {
   if (cc.valid) {
     const float2 p = cubic_pos(cc, float(row) - kCellMid);
@@ -153,7 +254,7 @@ __device__ __forceinline__ bool pixel_coords(const FwdPlan& P, const HP& Q, cons
     y = p.y;
     return true;
   }
-  return exact_coords(P, Q, a, dx, float(row - kCellH / 2), x, y);
+  return exact_coords(P, Q, a, float(lane - kAnchorCol), float(row) - kCellMid, x, y);
 }
 
 // Largest deviation of a valid column's positions from the straight line between two rows
@@ -195,12 +296,11 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HP& Q, const
   }
   nrows = min(nrows, Q.h - oy);
   const bool active = ox + lane < Q.w;
-  const float dx = float(Q.x0 + ox + lane - a.ax);
   float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f;
   bool ok = true;
   if (active) {
-    ok = pixel_coords(P, Q, a, cc, dx, r0, x0, y0);
-    ok = pixel_coords(P, Q, a, cc, dx, r0 + nrows - 1, x1, y1) && ok;
+    ok = pixel_coords(P, Q, a, cc, lane, r0, x0, y0);
+    ok = pixel_coords(P, Q, a, cc, lane, r0 + nrows - 1, x1, y1) && ok;
   }
   // (well inside the |v| < 2^22 range of the fast rows' floor by magic number)
   ok = ok && fabsf(x0) < 2097152.f && fabsf(y0) < 2097152.f && fabsf(x1) < 2097152.f &&
