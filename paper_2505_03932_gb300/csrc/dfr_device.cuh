@@ -556,8 +556,8 @@ __device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, float X, float 
 }
 
 // Anchor at target pixel position (X, Y) (absolute, exactly representable: integers or
-// quarter-integers). Not inlined: compiled once per translation unit.
-static __device__ __noinline__ void make_anchor(const FwdPlan& P, float X, float Y, Anchor& a) {
+// quarter-integers).
+__device__ __forceinline__ void make_anchor(const FwdPlan& P, float X, float Y, Anchor& a) {
   if (P.identity) {
     a.bx = int32_t(floorf(X));
     a.by = int32_t(floorf(Y));

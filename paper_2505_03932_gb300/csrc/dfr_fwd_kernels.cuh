@@ -198,8 +198,8 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
     for (int q = 0; q < T::n; ++q) {
       w[q].x = (unsigned(ix + q) < unsigned(W)) ? w[q].x : 0.f;
       w[q].y = (unsigned(iy + q) < unsigned(H)) ? w[q].y : 0.f;
-      sx += w[q].x;
-      sy += w[q].y;
+      sx = __fadd_rn(sx, w[q].x);
+      sy = __fadd_rn(sy, w[q].y);
     }
   }
   float num = 0.f;
@@ -214,7 +214,7 @@ __device__ __forceinline__ float2 interp_pixel(float x, float y, int bx, int by,
     num = k == 0 ? __fmul_rn(w[k].y, row) : fmaf(w[k].y, row, num);
   }
   if (interior) return make_float2(num, 1.f);
-  const float f = sx * sy;
+  const float f = __fmul_rn(sx, sy);
   if (f == 0.f) return make_float2(0.f, 0.f);
   return make_float2((f == 1.f) ? num : __fdividef(num, f), f);
 }
@@ -321,12 +321,20 @@ __device__ __forceinline__ uint32_t box_token() {
 // fractions, weights, and the tap sums, each half the exact operation sequence of the
 // per-pixel path (interp_pixel), so both give the same bits. The box pitch is the
 // compile-time kBoxW: a pixel's taps are immediate offsets from one shared address.
-template <int ORDER, bool ACC, int TH, bool FP>
+// EDGE: the tile's taps may leave the image (the box holds zeros there, the TMA fill): per pixel
+// also the coverage test and, unless all its taps are inside, the in-image weight sums as
+// footprint and value = sum / footprint, as interp_pixel does (the zero taps add nothing to
+// the sum, exactly like the zeroed weights there).
+template <int ORDER, bool ACC, int TH, bool FP, bool EDGE>
 __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a,
                                                     const ColCubic& cc, int gx, int oy, int r0,
                                                     uint32_t sbox, const TileBox& tb) {
   using T = Taps<ORDER>;
   constexpr int n = T::n;
+  // EDGE: absolute first-tap column/row = floor bits + (bx + lo - magic bits); coverage bounds
+  const int kxa = a.bx + T::lo - int(kFloorMagicBits), kya = a.by + T::lo - int(kFloorMagicBits);
+  const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
+  const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
   // shared address of a pixel's first tap: sbox + 4 ((floor(y) + by + lo - by0) kBoxW +
   // floor(x) + bx + lo - bx0), with the floors as bit patterns (modular arithmetic)
   const uint32_t kb = sbox + 4u * (uint32_t((a.by + T::lo - tb.by0) * kBoxW +
@@ -350,12 +358,14 @@ __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a
     uint32_t ia = __float_as_uint(my.x) * uint32_t(4 * kBoxW) + __float_as_uint(mx.x) * 4u + kb;
     uint32_t ib = __float_as_uint(my.y) * uint32_t(4 * kBoxW) + __float_as_uint(mx.y) * 4u + kb;
     float2 num;
+    float2 wx[n], wy[n];
+    auto wxs = [&](int q) { return wx[q]; };
+    auto wys = [&](int q) { return wy[q]; };
     if (ORDER == DFR_NEAREST) {
       ia += 4u * (uint32_t(tx.x >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.x >= 0.5f));
       ib += 4u * (uint32_t(tx.y >= 0.5f) + uint32_t(kBoxW) * uint32_t(ty.y >= 0.5f));
       num = make_float2(lds_f32(ia), lds_f32(ib));
     } else {
-      float2 wx[n], wy[n];
       if (ORDER == DFR_LANCZOS3) {
         float ax[6], bxw[6], ay[6], byw[6];
         lanczos3_weights<float>(tx.x, ax);
@@ -383,15 +393,52 @@ __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a
         num = k == 0 ? v_mul(wy[k], row) : v_fma(wy[k], row, num);
       }
     }
+    float2 fpv = make_float2(1.f, 1.f);
+    if (EDGE) {
+      // per pixel (half h = A, B): coverage, interior taps, else in-image weight sums
+      float v2[2] = {num.x, num.y}, f2[2] = {1.f, 1.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float xh_ = h ? X.y : X.x, yh_ = h ? Y.y : Y.x;
+        const float txh = h ? tx.y : tx.x, tyh = h ? ty.y : ty.x;
+        int ix = int(__float_as_uint(h ? mx.y : mx.x)) + kxa;
+        int iy = int(__float_as_uint(h ? my.y : my.x)) + kya;
+        if (ORDER == DFR_NEAREST) {
+          ix += txh >= 0.5f;
+          iy += tyh >= 0.5f;
+        }
+        const bool cov = xh_ >= xlo && xh_ <= xhi && yh_ >= ylo && yh_ <= yhi;
+        const bool inner = ix >= 0 && ix + n <= Q.W && iy >= 0 && iy + n <= Q.H;
+        float f = 1.f;
+        if (!inner) {
+          if (ORDER == DFR_NEAREST) {
+            f = 0.f;
+          } else {
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+              sx = __fadd_rn(sx, (unsigned(ix + q) < unsigned(Q.W)) ? (h ? wxs(q).y : wxs(q).x) : 0.f);
+              sy = __fadd_rn(sy, (unsigned(iy + q) < unsigned(Q.H)) ? (h ? wys(q).y : wys(q).x) : 0.f);
+            }
+            f = __fmul_rn(sx, sy);
+          }
+        }
+        const float v = v2[h];
+        v2[h] = (!cov || f == 0.f) ? 0.f : ((f == 1.f) ? v : __fdividef(v, f));
+        f2[h] = (!cov || f == 0.f) ? 0.f : f;
+      }
+      num = make_float2(v2[0], v2[1]);
+      fpv = make_float2(f2[0], f2[1]);
+    }
     if (ACC) {
-      put_pixel<true>(po, pf, num.x, 1.f);
-      put_pixel<true>(po + pitch, pf + pitch, num.y, 1.f);
+      put_pixel<true>(po, pf, num.x, fpv.x);
+      put_pixel<true>(po + pitch, pf + pitch, num.y, fpv.y);
     } else {
       __stcs(po, num.x);
       __stcs(po + pitch, num.y);
       if (FP) {
-        __stcs(pf, 1.f);
-        __stcs(pf + pitch, 1.f);
+        __stcs(pf, fpv.x);
+        __stcs(pf + pitch, fpv.y);
       }
     }
     po += 2 * pitch;
@@ -404,10 +451,17 @@ template <int ORDER, bool ACC, int TH>
 __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, const ColCubic& cc,
                                                int gx, int oy, int r0, uint32_t sbox,
                                                const TileBox& tb) {
-  if (ACC || Q.fp)
-    tile_rows_fast_impl<ORDER, ACC, TH, true>(Q, a, cc, gx, oy, r0, sbox, tb);
-  else
-    tile_rows_fast_impl<ORDER, ACC, TH, false>(Q, a, cc, gx, oy, r0, sbox, tb);
+  if (tb.interior) {
+    if (ACC || Q.fp)
+      tile_rows_fast_impl<ORDER, ACC, TH, true, false>(Q, a, cc, gx, oy, r0, sbox, tb);
+    else
+      tile_rows_fast_impl<ORDER, ACC, TH, false, false>(Q, a, cc, gx, oy, r0, sbox, tb);
+  } else {
+    if (ACC || Q.fp)
+      tile_rows_fast_impl<ORDER, ACC, TH, true, true>(Q, a, cc, gx, oy, r0, sbox, tb);
+    else
+      tile_rows_fast_impl<ORDER, ACC, TH, false, true>(Q, a, cc, gx, oy, r0, sbox, tb);
+  }
 }
 
 // General rows of a tile (per pixel): position (column cubic or exact), coverage, then the
@@ -557,6 +611,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
     Q.use_tma = Q.use_tma && !dead;
     const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
     const int gx = cox + lane;
+    prefetch_cell<ORDER>(P, Q, cox, coy, TH, NT, lane);
     Anchor a;
     const ColCubic cc = cell_fit(P, Q, cox, coy, lane, a);
     // fast rows need every column's cubic, bowing well inside the box margin
@@ -591,7 +646,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
       }
       const int oy = coy + t * TH;
       const float* bt = box + b * L.box_floats;
-      if (fast_cell && cur.use_box && cur.interior && oy + TH <= Q.h)
+      // fast rows: the box holds every tap (zeros outside the image); the B-spline's mirrored
+      // taps near the image edge take the general rows
+      if (fast_cell && cur.use_box && oy + TH <= Q.h &&
+          (cur.interior || ORDER != DFR_BSPLINE3))
         tile_rows_fast<ORDER, ACC, TH>(Q, a, cc, gx, oy, t * TH, smem_addr(bt) + tok, cur);
       else
         tile_rows<ORDER, ACC>(P, Q, a, cc, gx, oy, t * TH, TH, bt, cur);
