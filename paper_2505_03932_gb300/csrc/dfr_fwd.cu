@@ -45,34 +45,30 @@ cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s) {
 // ------------------------------------------------------------------ dispatch
 int forward_threads_default() { return kFp64Threads; }
 
-// Single-frame split kernel of a tile height (8, 16 or 32 rows).
 template <int ORDER>
-static const void* split_for(int th) {
-  switch (th) {
-    case 8: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 8>);
-    case 32: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 32>);
-    default: return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, false, 16>);
-  }
+static const void* fp64_for_order() {
+  return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, false>);
 }
 
-template <int ORDER>
-static const void* kernel_for_order(bool split, int th) {
-  if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, false>);
-  return split_for<ORDER>(th);
+// Split kernel of a launch form and tile height (8, 16 or 32 rows), from its instantiation unit.
+static const void* split_for(int order, bool batch, int th) {
+  if (batch) return th == 8 ? split_batch_t8(order) : th == 32 ? split_batch_t32(order)
+                                                               : split_batch_t16(order);
+  return th == 8 ? split_single_t8(order) : th == 32 ? split_single_t32(order)
+                                                     : split_single_t16(order);
 }
 
 // The kernel instantiation for a launch: order, flags and tile height are uniform over a
 // launch and taken from p0; batch launches read their plans from a table.
 static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
   if (p0.flags & kFlagAccumulate) return batch ? nullptr : coadd_kernel(p0);
-  const bool split = (p0.flags & DFR_SPLIT) != 0;
-  if (split && batch) return forward_batch_kernel(p0.order, p0.th);
+  if (p0.flags & DFR_SPLIT) return split_for(p0.order, batch, p0.th);
   switch (p0.order) {
-    case DFR_NEAREST: return kernel_for_order<DFR_NEAREST>(split, p0.th);
-    case DFR_BILINEAR: return kernel_for_order<DFR_BILINEAR>(split, p0.th);
-    case DFR_BICUBIC: return kernel_for_order<DFR_BICUBIC>(split, p0.th);
-    case DFR_LANCZOS3: return kernel_for_order<DFR_LANCZOS3>(split, p0.th);
-    default: return kernel_for_order<DFR_BSPLINE3>(split, p0.th);
+    case DFR_NEAREST: return fp64_for_order<DFR_NEAREST>();
+    case DFR_BILINEAR: return fp64_for_order<DFR_BILINEAR>();
+    case DFR_BICUBIC: return fp64_for_order<DFR_BICUBIC>();
+    case DFR_LANCZOS3: return fp64_for_order<DFR_LANCZOS3>();
+    default: return fp64_for_order<DFR_BSPLINE3>();
   }
 }
 

@@ -1200,8 +1200,13 @@ int dfr_device_status(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   e = read_and_clear_status_coadd(&d, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
-  e = read_and_clear_status_batch(&t, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+  for (auto rd : {split_single_t8_status, split_single_t16_status, split_single_t32_status,
+                  split_batch_t8_status, split_batch_t16_status, split_batch_t32_status}) {
+    int32_t u = 0;
+    e = rd(&u, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
+    t |= u;
+  }
   const int32_t s = a | b | c | d | t;
   if (s & kStatusTimeout) return fail(DFR_ERR_TIMEOUT, "a bounded device wait gave up");
   if (s & kStatusCheck) return fail(DFR_ERR_DEVICE, "a kernel reported a failed check");

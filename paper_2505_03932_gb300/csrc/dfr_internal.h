@@ -149,7 +149,13 @@ enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s);
 const void* forward_kernel(const FwdPlan& p0);
-const void* forward_batch_kernel(int order, int th);              // dfr_fwd_batch.cu
+// split kernels by launch form and tile height (dfr_fwd_{single,batch}_t{8,16,32}.cu)
+const void* split_single_t8(int order);
+const void* split_single_t16(int order);
+const void* split_single_t32(int order);
+const void* split_batch_t8(int order);
+const void* split_batch_t16(int order);
+const void* split_batch_t32(int order);
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s);
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
 int forward_threads_default();
@@ -157,7 +163,12 @@ cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd_tile(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_coadd(int32_t* out, cudaStream_t s);
-cudaError_t read_and_clear_status_batch(int32_t* out, cudaStream_t s);
+cudaError_t split_single_t8_status(int32_t* out, cudaStream_t s);
+cudaError_t split_single_t16_status(int32_t* out, cudaStream_t s);
+cudaError_t split_single_t32_status(int32_t* out, cudaStream_t s);
+cudaError_t split_batch_t8_status(int32_t* out, cudaStream_t s);
+cudaError_t split_batch_t16_status(int32_t* out, cudaStream_t s);
+cudaError_t split_batch_t32_status(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
