@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
       HP Q;
       if (split) {
         load_hot(P, Q);
-        cc = cell_fit<false>(P, Q, ox, gy - gy % kCellH, lane, a);
+        cc = cell_fit<false, true>(P, Q, ox, gy - gy % kCellH, lane, a);
       }
       bool cov = false;
       int bx = 0, by = 0;

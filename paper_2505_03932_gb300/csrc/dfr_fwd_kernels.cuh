@@ -611,7 +611,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
     Q.use_tma = Q.use_tma && !dead;
     const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
     const int gx = cox + lane;
-    prefetch_cell<ORDER>(P, Q, cox, coy, TH, NT, lane);
     Anchor a;
     const ColCubic cc = cell_fit(P, Q, cox, coy, lane, a);
     // fast rows need every column's cubic, bowing well inside the box margin

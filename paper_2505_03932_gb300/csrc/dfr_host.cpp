@@ -314,61 +314,6 @@ void size_box(FwdPlan& P) {
                                 (4 * hh * hh));
       }
     }
-  // affine approximation of the map (least squares over the same grid), for L2 prefetches
-  {
-    double Sm[3][3] = {{0}}, Sx[3] = {0}, Sy[3] = {0};
-    std::vector<double> us, vs, xs, ys;
-    for (int j = 0; j < ns; ++j)
-      for (int i = 0; i < ns; ++i) {
-        const double u = (P.w - 1) * double(i) / (ns - 1), v = (P.h - 1) * double(j) / (ns - 1);
-        double x, y;
-        if (!M.eval(P.x0 + u, P.y0 + v, x, y)) continue;
-        const double r[3] = {u, v, 1.0};
-        for (int a = 0; a < 3; ++a) {
-          for (int b = 0; b < 3; ++b) Sm[a][b] += r[a] * r[b];
-          Sx[a] += r[a] * x;
-          Sy[a] += r[a] * y;
-        }
-        us.push_back(u);
-        vs.push_back(v);
-        xs.push_back(x);
-        ys.push_back(y);
-      }
-    P.aff_r = -1.f;
-    // 3x3 solve by Cramer's rule (the grid spans the box: well conditioned)
-    auto det3 = [](const double m[3][3]) {
-      return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
-             m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
-             m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
-    };
-    const double D = det3(Sm);
-    if (us.size() >= 9 && std::fabs(D) > 0.0 && std::isfinite(D)) {
-      double cx[3], cy[3];
-      for (int k = 0; k < 3; ++k) {
-        double mx[3][3], my[3][3];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            mx[a][b] = (b == k) ? Sx[a] : Sm[a][b];
-            my[a][b] = (b == k) ? Sy[a] : Sm[a][b];
-          }
-        cx[k] = det3(mx) / D;
-        cy[k] = det3(my) / D;
-      }
-      double res = 0.0;
-      for (size_t k = 0; k < us.size(); ++k) {
-        res = std::max(res, std::fabs(cx[0] * us[k] + cx[1] * vs[k] + cx[2] - xs[k]));
-        res = std::max(res, std::fabs(cy[0] * us[k] + cy[1] * vs[k] + cy[2] - ys[k]));
-      }
-      // a prediction more than a box margin off brings the wrong lines: no prefetch then
-      if (std::isfinite(res) && res < 16.0) {
-        for (int k = 0; k < 3; ++k) {
-          P.aff[k] = float(cx[k]);
-          P.aff[3 + k] = float(cy[k]);
-        }
-        P.aff_r = float(res + 1.0);
-      }
-    }
-  }
   P.jac[0] = float(jxx);
   P.jac[1] = float(jxy);
   P.jac[2] = float(jyx);

@@ -66,10 +66,6 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   int32_t tma_ok;            // the source allows TMA (16-byte aligned base and pitch)
   float jac[4];              // host bounds of |dx/dX|, |dx/dY|, |dy/dX|, |dy/dY| (box sizing)
   float curv[3];             // host bounds of the map's second derivatives (xx, xy, yy)
-  float aff[6];              // affine approximation of the map over the bounding box:
-                             // x = aff0 u + aff1 v + aff2, y = aff3 u + aff4 v + aff5 (u, v:
-                             // bounding-box pixel), for L2 prefetches
-  float aff_r;               // its largest residual on the sampled grid, px (< 0: none)
   int32_t identity;          // source and target WCS are bitwise equal
   // target WCS
   double crpix_t[2];         // CRPIX - 1 (0-based reference pixel)

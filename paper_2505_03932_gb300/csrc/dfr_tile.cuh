@@ -170,16 +170,21 @@ __device__ __forceinline__ float2 cell_sample(int k) {
 // Exact source position at cell point (sx, s): the anchor there and its own offset-0 position
 // (relative to that anchor's base). Inlined (with the plan read as kernel-parameter operands
 // where the plan is the parameter): the fit's latency is on every cell's critical path.
-__device__ __forceinline__ bool cell_point(const FwdPlan& P, const HP& Q, float X, float Y,
-                                           Anchor& an, float& x, float& y) {
+// Every variant (target SIP, Newton inverse, identity), not inlined: compiled once per
+// translation unit (the adjoint kernels, and the rare plans of the forward ones).
+static __device__ __noinline__ bool cell_point_call(const FwdPlan& P, const HP& Q, float X,
+                                                    float Y, Anchor& an, float& x, float& y) {
   make_anchor(P, X, Y, an);
   return exact_coords_t<true>(P, Q, an, 0.f, 0.f, x, y, nullptr);
 }
 
-// The same, not inlined (the adjoint kernels: compiled once per translation unit).
-static __device__ __noinline__ bool cell_point_call(const FwdPlan& P, const HP& Q, float X,
-                                                    float Y, Anchor& an, float& x, float& y) {
-  return cell_point(P, Q, X, Y, an, x, y);
+// The common plan (no target SIP, polynomial or no inverse SIP) inlined: the double-float
+// anchor and the inverse SIP by the rolled runtime-degree Horner, whose FMA sequence (and so
+// every bit) is that of the unrolled forms cell_point_call takes.
+__device__ __forceinline__ bool cell_point(const FwdPlan& P, const HP& Q, float X, float Y,
+                                           Anchor& an, float& x, float& y) {
+  make_anchor(P, X, Y, an);
+  return exact_coords_t<true>(P, Q, an, 0.f, 0.f, x, y, nullptr);
 }
 
 __device__ __forceinline__ Anchor shfl_anchor(const Anchor& a, int src) {
@@ -207,7 +212,9 @@ __device__ __forceinline__ Anchor shfl_anchor(const Anchor& a, int src) {
 // Warp-collective (all 32 lanes, lane = column): the cell's anchor and this lane's column
 // cubic. (cox, coy): the cell's first column and row in the bounding box. INL: the sample
 // evaluation inlined (forward kernels) or called (adjoint kernels); the same bits either way.
-template <bool INL = true>
+// FULL: every anchor field for every cell (the adjoint's chain rule needs them); otherwise only
+// its integer base where the cell's cubics are valid.
+template <bool INL = true, bool FULL = false>
 __device__ __forceinline__ ColCubic cell_fit(const FwdPlan& P, const HP& Q, int cox, int coy,
                                              int lane, Anchor& anchor) {
   const unsigned full = 0xffffffffu;
@@ -219,10 +226,11 @@ __device__ __forceinline__ ColCubic cell_fit(const FwdPlan& P, const HP& Q, int 
     const float X = float(Q.x0 + cox) + (p.x + 15.5f), Y = float(Q.y0 + coy) + (p.y + kCellMid);
     ok = INL ? cell_point(P, Q, X, Y, an, x, y) : cell_point_call(P, Q, X, Y, an, x, y);
   }
-  anchor = shfl_anchor(an, 16);
+  // the anchor's integer base (the whole anchor further down, where the cubics do not serve)
+  const int abx = __shfl_sync(full, an.bx, 16), aby = __shfl_sync(full, an.by, 16);
   // sample positions relative to the anchor's base
   if (lane < 20) {
-    const int ox = an.bx - anchor.bx, oy = an.by - anchor.by;
+    const int ox = an.bx - abx, oy = an.by - aby;
     ok = ok && abs(ox) < (1 << 20) && abs(oy) < (1 << 20);
     x = __fadd_rn(x, float(ox));
     y = __fadd_rn(y, float(oy));
@@ -255,6 +263,12 @@ __device__ __forceinline__ ColCubic cell_fit(const FwdPlan& P, const HP& Q, int 
     }
   }
   cc.valid = __all_sync(full, ok && chk) && !Q.identity;
+  if (cc.valid && !FULL) {
+    anchor.bx = abx;
+    anchor.by = aby;
+  } else {
+    anchor = shfl_anchor(an, 16);
+  }
   return cc;
 }
 
@@ -281,44 +295,6 @@ __device__ __forceinline__ float cubic_bow(const ColCubic& cc, int h) {
   const float bx = fmaf(6.f * kNodeA, fabsf(cc.c[3].x), 2.f * fabsf(cc.c[2].x));
   const float by = fmaf(6.f * kNodeA, fabsf(cc.c[3].y), 2.f * fabsf(cc.c[2].y));
   return hh * fmaxf(bx, by);
-}
-
-// L2 prefetch of the source boxes of a cell's tiles before the cell is fitted: the box of tile
-// lane (lanes 0 .. nt-1) as the plan's affine approximation of the map predicts it (host
-// least-squares fit over the bounding box, aff_r its largest residual), widened like the real
-// box. Only brings lines into L2 (nothing is written to shared memory), so a wrong
-// prediction costs bandwidth, never correctness.
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int32_t x, int32_t y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y)
-               : "memory");
-}
-
-template <int ORDER>
-__device__ __forceinline__ void prefetch_cell(const FwdPlan& P, const HP& Q, int cox, int coy,
-                                              int th, int nt, int lane) {
-  using T = Taps<ORDER>;
-  if (!Q.use_tma || !(P.aff_r >= 0.f) || lane >= nt) return;
-  const float u0 = float(cox), u1 = float(cox + kCellW - 1);
-  const float v0 = float(coy + lane * th), v1 = float(coy + lane * th + th - 1);
-  float xl = 3.4e38f, xh = -3.4e38f, yl = 3.4e38f, yh = -3.4e38f;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float u = (c & 1) ? u1 : u0, v = (c & 2) ? v1 : v0;
-    const float xs = fmaf(P.aff[0], u, fmaf(P.aff[1], v, P.aff[2]));
-    const float ys = fmaf(P.aff[3], u, fmaf(P.aff[4], v, P.aff[5]));
-    xl = fminf(xl, xs);
-    xh = fmaxf(xh, xs);
-    yl = fminf(yl, ys);
-    yh = fmaxf(yh, ys);
-  }
-  const float m = P.aff_r + float(max(1, P.box_margin) - T::lo);
-  const int x_lo = int(floorf(xl - m)), y_lo = int(floorf(yl - m));
-  if (!(xh + m >= 0.f && yh + m >= 0.f && xl - m < float(Q.W) && yl - m < float(Q.H))) return;
-  // a start inside the image, x on a 16-byte boundary
-  const int x = min(max(x_lo, 0), Q.W - 1) & ~3, y = min(max(y_lo, 0), Q.H - 1);
-  tma_prefetch_2d(&P.tmap, x, y);
 }
 
 // Source box of the tile of rows [r0, r0 + nrows) of a cell (columns ox .. ox + 31, first row
