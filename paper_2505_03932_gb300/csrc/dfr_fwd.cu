@@ -96,10 +96,10 @@ cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int 
   return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, size_t(smem_bytes), s);
 }
 
-int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes) {
+int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes, bool batch) {
   (void)threads;
   threads = block_threads(p0);
-  const void* k = forward_kernel_for(p0, true);
+  const void* k = forward_kernel_for(p0, batch);
   if (smem_bytes > 0)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   int nb = 0;

@@ -591,9 +591,18 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
   bool dead = false;     // a wait gave up: no more copies from this warp
   constexpr bool batch = BATCH;
   constexpr int NT = kCellH / TH;
-  // cells; a single-frame launch may cover cells [unit_begin, unit_begin + grid) only (bands)
+  // cells; a single-frame launch may cover cells [unit_begin, unit_begin + grid) only (bands).
+  // Single-frame launches may split the cells of their last partial wave (from cell
+  // split_from on) into split_k work units of NT / split_k tiles each.
   const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
   int id = blockIdx.x + L.unit_begin;
+  int t0 = 0, t1 = NT;
+  if (!batch && L.split_k > 1 && id >= L.split_from) {
+    const int u = id - L.split_from, part = u % L.split_k;
+    id = L.split_from + u / L.split_k;
+    t0 = part * (NT / L.split_k);
+    t1 = t0 + NT / L.split_k;
+  }
   if (batch) {
     int t = 0;
     if (lane == 0) t = atomicAdd(L.counter, 1);
@@ -617,15 +626,16 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
     const bool fast_cell = !Q.mask && cc.valid &&
                            __all_sync(0xffffffffu, cubic_bow(cc, TH) <= 0.5f) &&
                            cox + kCellW <= Q.w;
-    TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy, 0, TH, lane, box, &bar[0], batch, true,
+    TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy + t0 * TH, t0 * TH, TH, lane,
+                                  box + (t0 & 1) * L.box_floats, &bar[t0 & 1], batch, true,
                                   L.tx_extra);
-    if (cur.use_box) pending |= 1u;
-    prefetch_sums<ACC>(Q, cox, coy, TH, lane);
-    for (int t = 0; t < NT; ++t) {
+    if (cur.use_box) pending |= 1u << (t0 & 1);
+    prefetch_sums<ACC>(Q, cox, coy + t0 * TH, TH, lane);
+    for (int t = t0; t < t1; ++t) {
       const int b = t & 1;
       TileBox nxt;
       nxt.use_box = false;
-      if (t + 1 < NT) {
+      if (t + 1 < t1) {
         nxt = tile_box<ORDER>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
                               box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch, true, L.tx_extra);
         if (nxt.use_box) pending |= 1u << (b ^ 1);

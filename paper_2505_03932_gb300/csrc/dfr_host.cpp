@@ -711,6 +711,46 @@ uint32_t fault_tx_extra() {
   return v;
 }
 
+// Work units of a single-frame split launch over `cells` one-cell CTAs: the cells that fill whole
+// waves of resident CTAs stay whole; the cells of the last partial wave (all of them when the
+// frame fills less than a wave) are split into k units of fewer tiles (k a power of two up to
+// the tiles per cell, the smallest that fills a wave), so that the launch does not end on a
+// thin wave of long CTAs. Returns the grid; sets split_from and split_k.
+int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int>, int> occ;
+  split_from = cells;
+  split_k = 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cells;
+  const int smem = smem_for(P);
+  const void* k = forward_kernel(P);
+  const auto key = std::make_tuple(dev, k, smem);
+  int n = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = occ.find(key);
+    if (it != occ.end()) n = it->second;
+  }
+  if (n == 0) {
+    n = forward_max_blocks_per_sm(P, kFwdWarps * 32, smem, false);
+    std::lock_guard<std::mutex> lock(mu);
+    occ[key] = n;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cells;
+  const int slots = std::max(1, sms * n);
+  const int rest = cells % slots;
+  const int nt = kCellH / std::max(1, P.th);
+  if (rest == 0) return cells;
+  int kk = 1;
+  while (kk < nt && rest * kk < slots) kk *= 2;
+  if (kk == 1) return cells;
+  split_from = cells - rest;
+  split_k = kk;
+  return split_from + rest * kk;
+}
+
 // One single-frame launch of a plan (grid of work units, dynamic shared memory for the boxes).
 cudaError_t launch_single(const FwdPlan& P, cudaStream_t s) {
   FwdLaunch L{};
@@ -719,10 +759,10 @@ cudaError_t launch_single(const FwdPlan& P, cudaStream_t s) {
   int grid = L.total_tiles;
   FwdPlan Pk = P;
   if (P.flags & DFR_SPLIT) {
-    // work units of kCellsPerCta anchor cells, one per CTA; the coordinate output is a
-    // separate kernel (same arithmetic)
+    // one cell per CTA (the last partial wave split, see tail_split); the coordinate output is
+    // a separate kernel (same arithmetic)
     L.total_tiles = P.cells_x * P.cells_y;
-    grid = (L.total_tiles + kCellsPerCta - 1) / kCellsPerCta;
+    grid = tail_split(P, L.total_tiles, L.split_from, L.split_k);
     L.tx_extra = fault_tx_extra();
     Pk.coords = nullptr;
   }

@@ -112,6 +112,8 @@ struct FwdLaunch {
   int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
   int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
   int32_t unit_begin;        // single-frame split launch: first work unit (a band of the box)
+  int32_t split_from;        // single frame: cells from this one on are split into split_k
+  int32_t split_k;           // units of kCellH / (TH split_k) tile rows each (1: no split)
   uint32_t tx_extra;         // fault injection for the timeout test: bytes added to every box
                              // load's expected count, so that its wait runs out (0 normally)
 };
@@ -153,7 +155,7 @@ const void* split_batch_t8(int order);
 const void* split_batch_t16(int order);
 const void* split_batch_t32(int order);
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s);
-int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes);
+int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes, bool batch = true);
 int forward_threads_default();
 cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
