@@ -209,6 +209,30 @@ def _dev_f32(t, name):
     return t
 
 
+def _naxis(w):
+    nax = w.naxis if isinstance(w, DfrWcs) else w["naxis"]
+    return int(nax[0]), int(nax[1])
+
+
+def _check_image(img, wcs, name):
+    """The kernels read NAXIS2 rows of NAXIS1 pixels at the tensor's row stride: refuse a smaller
+    tensor (it would be read past its end)."""
+    nx, ny = _naxis(wcs)
+    if img.shape[0] < ny or img.shape[1] < nx:
+        raise ValueError("%s has shape %s, smaller than the WCS NAXIS (%d, %d)"
+                         % (name, tuple(img.shape), ny, nx))
+
+
+def _check_out(out, fp, w, h, name="out"):
+    """Value and footprint planes of a (w, h) bounding box: at least h rows of w pixels, and the
+    footprint the same shape and row stride (the library takes one pitch for both)."""
+    if out.shape[0] < h or out.shape[1] < w:
+        raise ValueError("%s has shape %s, smaller than the box (%d, %d)"
+                         % (name, tuple(out.shape), h, w))
+    if fp is not None and (tuple(fp.shape) != tuple(out.shape) or fp.stride(0) != out.stride(0)):
+        raise ValueError("the footprint must have the shape and row stride of %s" % name)
+
+
 def _flags(precision, exact_inverse, tma, nan_mask=False):
     f = SPLIT if precision == "split" else FP64
     if precision not in ("split", "fp64"):
@@ -259,7 +283,9 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
     prefilters the image first unless ``prefiltered`` (then src_img holds the coefficients).
     Returns (value, footprint or None[, coords (h, w, 2) float64])."""
     torch = _torch()
-    src_img = _source_for(_dev_f32(src_img, "src_img"), order, prefiltered, stream)
+    src_img = _dev_f32(src_img, "src_img")
+    _check_image(src_img, src_wcs, "src_img")
+    src_img = _source_for(src_img, order, prefiltered, stream)
     if bbox is None:
         if shape_out is None:
             nax = tgt_wcs.naxis if isinstance(tgt_wcs, DfrWcs) else tgt_wcs["naxis"]
@@ -274,6 +300,7 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
     if footprint:
         fp = fp_out if fp_out is not None else torch.empty((h, w), dtype=torch.float32, device=dev)
         fp = _dev_f32(fp, "footprint")
+    _check_out(out, fp, w, h)
     cr = torch.empty((h, w, 2), dtype=torch.float64, device=dev) if coords else None
     _check(lib().dfr_reproject(
         ctypes.byref(to_c(src_wcs)), ctypes.byref(to_c(tgt_wcs)), ctypes.c_void_p(src_img.data_ptr()),
@@ -286,7 +313,7 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
 
 def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear",
                     precision="split", outs=None, fps=None, footprint=True, stream=None,
-                    nan_mask=False, prefiltered=False):
+                    nan_mask=False, prefiltered=False, tma=True):
     """Reproject many exposures in one persistent launch (dfr_reproject_batch).
 
     bboxes default to dfr_target_bbox per frame. Returns (values, footprints) lists."""
@@ -295,15 +322,20 @@ def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear"
     frames = (DfrFrame * max(n, 1))()
     vals, fpl, keep = [], [], []
     for i in range(n):
-        img = _source_for(_dev_f32(images[i], "images[%d]" % i), order, prefiltered, stream)
+        img = _dev_f32(images[i], "images[%d]" % i)
+        _check_image(img, src_wcs_list[i], "images[%d]" % i)
+        img = _source_for(img, order, prefiltered, stream)
         keep.append(img)
         bb = bboxes[i] if bboxes is not None else target_bbox(src_wcs_list[i], tgt_wcs)
         x0, y0, w, h = (int(v) for v in bb)
         o = outs[i] if outs is not None else torch.empty((max(h, 1), max(w, 1)),
                                                           dtype=torch.float32, device=img.device)
+        o = _dev_f32(o, "outs[%d]" % i)
         f = None
         if footprint:
             f = fps[i] if fps is not None else torch.empty_like(o)
+            f = _dev_f32(f, "fps[%d]" % i)
+        _check_out(o, f, w, h, "outs[%d]" % i)
         fr = frames[i]
         fr.wcs = to_c(src_wcs_list[i])
         fr.img = img.data_ptr()
@@ -315,23 +347,31 @@ def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear"
         vals.append(o)
         fpl.append(f)
     _check(lib().dfr_reproject_batch(frames, n, ctypes.byref(to_c(tgt_wcs)), _order(order),
-                                     _flags(precision, False, True, nan_mask),
+                                     _flags(precision, False, tma, nan_mask),
                                      _stream_ptr(stream)))
     return vals, fpl
 
 
 def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=None,
-                            order="bilinear", precision="split", stream=None):
+                            order="bilinear", precision="split", stream=None, prefiltered=False,
+                            tma=True):
     """dfr_reproject_batch_noalloc: the batched reprojection for callers that cannot allocate
     device memory. The library keeps its frame table in a fixed device array (at most 64
     frames per call) instead of calling cudaMalloc; the caller passes every image and output
-    buffer (``outs``, optional ``fps``). Returns (outs, fps)."""
+    buffer (``outs``, optional ``fps``). For order "bspline3" the images must already hold the
+    B-spline coefficients (``prefiltered=True``: the prefilter needs scratch memory, so this
+    entry point does not run it). Returns (outs, fps)."""
+    if _order(order) == BSPLINE3 and not prefiltered:
+        raise ValueError("reproject_batch_noalloc with order bspline3 takes prefiltered "
+                         "coefficients (prefiltered=True); see bspline_prefilter")
     n = len(images)
     frames = (DfrFrame * max(n, 1))()
     for i in range(n):
         img = _dev_f32(images[i], "images[%d]" % i)
+        _check_image(img, src_wcs_list[i], "images[%d]" % i)
         o = _dev_f32(outs[i], "outs[%d]" % i)
         f = _dev_f32(fps[i], "fps[%d]" % i) if fps is not None else None
+        _check_out(o, f, int(bboxes[i][2]), int(bboxes[i][3]), "outs[%d]" % i)
         fr = frames[i]
         fr.wcs = to_c(src_wcs_list[i])
         fr.img = img.data_ptr()
@@ -341,7 +381,7 @@ def reproject_batch_noalloc(images, src_wcs_list, tgt_wcs, bboxes, outs, fps=Non
         fr.out_pitch = o.stride(0)
         fr.x0, fr.y0, fr.w, fr.h = (int(v) for v in bboxes[i])
     _check(lib().dfr_reproject_batch_noalloc(frames, n, ctypes.byref(to_c(tgt_wcs)),
-                                             _order(order), _flags(precision, False, True),
+                                             _order(order), _flags(precision, False, tma),
                                              _stream_ptr(stream)))
     return outs, fps
 
@@ -370,7 +410,9 @@ def coadd(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear", precisio
     frames = (DfrFrame * max(n, 1))()
     keep = []
     for i in range(n):
-        img = _source_for(_dev_f32(images[i], "images[%d]" % i), order, prefiltered, stream)
+        img = _dev_f32(images[i], "images[%d]" % i)
+        _check_image(img, src_wcs_list[i], "images[%d]" % i)
+        img = _source_for(img, order, prefiltered, stream)
         keep.append(img)
         fr = frames[i]
         fr.wcs = to_c(src_wcs_list[i])
@@ -413,12 +455,15 @@ def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinea
     ``tma=False`` selects the per-pixel kernel (no staged source / gradient boxes)."""
     torch = _torch()
     src_img = _dev_f32(src_img, "src_img")
+    _check_image(src_img, src_wcs, "src_img")
     grad_out = _dev_f32(grad_out, "grad_out")
     x0, y0, w, h = (int(v) for v in bbox)
+    _check_out(grad_out, None, w, h, "grad_out")
     gs = None
     if want_src:
         gs = grad_src if grad_src is not None else torch.zeros_like(src_img)
         gs = _dev_f32(gs, "grad_src")
+        _check_image(gs, src_wcs, "grad_src")
     gp = torch.zeros(num_params(src_wcs), dtype=torch.float64, device=src_img.device) \
         if want_params else None
     _check(lib().dfr_reproject_backward(
@@ -466,6 +511,10 @@ def reproject_host(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="
     if not isinstance(src_img, np.ndarray) and not hasattr(src_img, "data_ptr"):
         src_img = np.ascontiguousarray(src_img, dtype=np.float32)
     ip, istride = _host_ptr(src_img, "src_img")
+    nx, ny = _naxis(src_wcs)
+    if src_img.shape[0] < ny or src_img.shape[1] < nx:
+        raise ValueError("src_img has shape %s, smaller than the WCS NAXIS (%d, %d)"
+                         % (tuple(src_img.shape), ny, nx))
     if out is None:
         out = np.empty((h, w), np.float32)
     op, ostride = _host_ptr(out, "out", (h, w))

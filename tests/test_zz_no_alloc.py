@@ -1,9 +1,9 @@
 """dfr_reproject_batch_noalloc through the C ABI: the batched reprojection for callers that
 cannot allocate device memory (it keeps its frame table in a fixed library-owned device array
-instead of calling cudaMalloc). Its output must match dfr_reproject_batch's within the value
-tolerance the parity tests use, on two calls in a row (the second call reuses the array that
-the first one left behind). This file is collected last on purpose."""
-import numpy as np
+instead of calling cudaMalloc). Its output must equal dfr_reproject_batch's bit for bit, as its
+declaration promises, on two calls in a row (the second call reuses the array that the first
+one left behind), for both precisions, with and without TMA staging. This file is collected
+last on purpose."""
 import pytest
 
 import synth
@@ -11,7 +11,6 @@ from oracle import wcs as OW
 
 pytestmark = pytest.mark.gpu
 
-VALUE_RTOL = 1e-5
 
 
 def _inputs(seed):
@@ -29,7 +28,9 @@ def _inputs(seed):
     return srcs, imgs, tgt
 
 
-def test_noalloc_batch_matches_batch_twice():
+@pytest.mark.parametrize("tma", [True, False])
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_noalloc_batch_matches_batch_twice(precision, tma):
     import torch
     import paper_2505_03932_gb300 as dfr
 
@@ -38,16 +39,17 @@ def test_noalloc_batch_matches_batch_twice():
         imgs_d = [torch.from_numpy(i).cuda() for i in imgs]
         bbs = [dfr.target_bbox(s, tgt) for s in srcs]
         for order in ("bilinear", "bicubic"):
-            ref_v, ref_f = dfr.reproject_batch(imgs_d, srcs, tgt, bbs, order=order)
+            ref_v, ref_f = dfr.reproject_batch(imgs_d, srcs, tgt, bbs, order=order,
+                                               precision=precision, tma=tma)
             outs = [torch.full((bb[3], bb[2]), -1.0, device="cuda") for bb in bbs]
             fps = [torch.full((bb[3], bb[2]), -1.0, device="cuda") for bb in bbs]
-            dfr.reproject_batch_noalloc(imgs_d, srcs, tgt, bbs, outs, fps, order=order)
+            dfr.reproject_batch_noalloc(imgs_d, srcs, tgt, bbs, outs, fps, order=order,
+                                        precision=precision, tma=tma)
             torch.cuda.synchronize()
             dfr.device_status()
             for k in range(len(srcs)):
-                a, b = outs[k].cpu().numpy(), ref_v[k].cpu().numpy()
-                assert np.all(np.abs(a - b) <= VALUE_RTOL * np.maximum(np.abs(b), 1.0)), (call, k)
-                assert np.all(np.abs(fps[k].cpu().numpy() - ref_f[k].cpu().numpy()) <= 1e-6)
+                assert torch.equal(outs[k], ref_v[k]), (call, order, k)
+                assert torch.equal(fps[k], ref_f[k]), (call, order, k)
 
 
 def test_noalloc_rejects_more_than_64_frames():
