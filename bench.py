@@ -123,6 +123,32 @@ def _recorded():
     return {}
 
 
+def recorded_fp64():
+    """FP64 flops per output pixel of the all-FP64 kernel (ncu SASS counts: 2 per DFMA, 1 per
+    DADD and DMUL) from the committed summary, or None when the FP64 kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "fp64_bicubic_4096.md")
+    try:
+        rec = {}
+        for line in open(path):
+            k, sep, v = line.partition(":")
+            if sep and k in ("fp64_flops_per_pixel", "fp64_source_sha256"):
+                rec[k] = v.strip()
+        if rec.get("fp64_source_sha256") == fp64_source_hash():
+            return float(rec["fp64_flops_per_pixel"])
+    except Exception:
+        pass
+    return None
+
+
+def fp64_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dfr_fwd_kernels.cuh", "dfr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the bench kernel (ncu), or None (kernel changed since)."""
     rec = _recorded()
@@ -289,9 +315,25 @@ def run_gpu(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the timed region
+
+    def soak(seconds):
+        """Back-to-back bench steps (with the flush) for about `seconds` of device time: the
+        continuous load around the timed steps, so that the clock sampler sees the GPU under
+        the bench's own load before, during and after them."""
+        n = 0
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            for _ in range(64):
+                flush.fill_(1.0)
+                step()
+            n += 64
+            torch.cuda.synchronize()
+        return n
+
     for _ in range(max(args.warmup, 3)):  # the GPU idled during the sleep: warm up again
         flush.fill_(1.0)
         step()
+    soak_before = soak(0.6)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -299,7 +341,11 @@ def run_gpu(args, rank, world, local_rank):
     t0 = time.perf_counter()
     times = timed(args.steps, "split")
     wall = time.perf_counter() - t0
+    soak_after = soak(0.3)
     clk = clocks.stop()
+    clk["window"] = ("%d steps of continuous load before and %d after the %d timed ones"
+                     % (soak_before, soak_after, args.steps))
+    tuned = dfr.last_launch_config()["single_tile_h"]
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -310,11 +356,20 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
-    # the plain all-FP64 GPU path on the same workload (its own, shorter timing)
+    # the plain all-FP64 GPU path on the same workload (its own, shorter timing), and the
+    # measured pipe peaks that bound it
     for _ in range(2):
         step("fp64")
     torch.cuda.synchronize()
     ms64 = float(np.mean(timed(max(3, min(args.steps, 5)), "fp64")))
+    pipes = dfr.measure_pipe_peaks()
+    f64 = recorded_fp64()
+    fp64_roof = None
+    if f64 is not None:
+        ach = f64 * npix / (ms64 * 1e-3)
+        fp64_roof = {"bound": "fp64", "achieved": ach / 1e12, "peak": pipes["fp64_fma_flops"] / 1e12,
+                     "unit": "TFLOP/s", "frac": ach / pipes["fp64_fma_flops"],
+                     "fp64_flops_per_pixel": f64, "peak_source": "measured (dfr_measure_pipe_peaks)"}
 
     # split vs FP64 coordinate difference over the frame (both GPU paths, FP64 emitted coords)
     _, _, c32 = dfr.reproject(img_d, src, tgt, bbox=(0, 0, W, H), order="bicubic",
@@ -369,6 +424,11 @@ def run_gpu(args, rank, world, local_rank):
                "single_core": {"value": npx1 / secs1 / 1e6, "unit": "Mpix/s",
                                "sample": "%d random target pixels (%.1f s)" % (npx1, secs1)}}
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["batch64"] = measure_batch64(dfr, torch, flush, max(3, min(args.steps, 10)))
+        extra["adjoint2048"] = measure_adjoint2048(dfr, torch, flush, max(3, min(args.steps, 10)))
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
@@ -378,14 +438,17 @@ def run_gpu(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "split", "output_mpix": npix / 1e6,
-                       "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
+                       "l2": "flushed between steps (512 MB write)", "parallelism": "replicas",
+                       "tile": "32 x %d target pixels per staged source box (tuned)" % tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "issue": recorded_issue(),
                          "peak_source": peak_src,
                          "bytes_per_pixel": BYTES_PER_PIX},
             "fp64_path": {"ms_per_step": ms64, "value": npix / (ms64 * 1e-3) / 1e6,
-                          "unit": "Mpix/s", "split_speedup": ms64 / ms},
+                          "unit": "Mpix/s", "split_speedup": ms64 / ms, "roofline": fp64_roof},
+            "pipe_peaks": {k: v / 1e12 for k, v in pipes.items()},
+            "pipe_peaks_unit": "T per second (flops, or special-function results)",
             "split_vs_fp64_px": {"max": dmax, "rms": drms},
             "inverse_sip_fit_px": {"max": fit_max, "rms": fit_rms},
             "e2e": {"value": npix * world / e2e_s / 1e6, "unit": "Mpix/s",
@@ -396,6 +459,7 @@ def run_gpu(args, rank, world, local_rank):
             "timed_wall_s": wall,
             "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
 
 
@@ -419,6 +483,78 @@ def _events_time(fn, k, flush=None):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
     return float(np.median(ts)), float(np.median(hs))
+
+
+def measure_batch64(dfr, torch, flush, steps):
+    """The batch configuration: 64 exposures (long side 2048-6144 px, SIP3) onto one 8192^2
+    target, bilinear, split precision, value and footprint; dfr_reproject_batch (one CUDA-graph
+    or persistent launch, tuned on the first call) against 64 separate dfr_reproject calls."""
+    c = synth.config2()
+    tgt = dfr.to_c(c["tgt"])
+    srcs = [dfr.to_c(dfr.fit_inverse_sip(sw, 4)[0]) for sw in c["src"]]
+    imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
+    src_bytes = sum(i.numel() * 4 for i in imgs)
+    del c
+    bbs = [dfr.target_bbox(sw, tgt) for sw in srcs]
+    outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
+    fps = [torch.empty_like(o) for o in outs]
+    npx = sum(b[2] * b[3] for b in bbs)
+    batch = lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bilinear", outs=outs,
+                                        fps=fps)
+    batch()  # the first call of this kind tunes the launch
+    torch.cuda.synchronize()
+    cfg = dfr.last_launch_config()["batch"]
+    t_batch, h_batch = _events_time(batch, steps, flush)
+
+    def separate():
+        for k in range(len(imgs)):
+            dfr.reproject(imgs[k], srcs[k], tgt, bbox=bbs[k], order="bilinear", out=outs[k],
+                          fp_out=fps[k])
+    separate()
+    t_sep, h_sep = _events_time(separate, steps, flush)
+    dfr.device_status()
+    peak = _peaks()[0]
+    # algorithmic bytes: every source pixel read once, value and footprint written
+    algo = src_bytes + 8 * npx
+    return {"workload": "64 frames (2048-6144 px, SIP3) -> 8192^2, bilinear, split",
+            "output_mpix": npx / 1e6, "ms": t_batch, "host_call_ms": h_batch,
+            "separate_launches_ms": t_sep, "mpix_s": npx / t_batch / 1e3,
+            "separate_mpix_s": npx / t_sep / 1e3, "speedup_vs_separate": t_sep / t_batch,
+            "roofline": {"bound": "hbm", "achieved": algo / (t_batch * 1e-3) / 1e9,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": algo / (t_batch * 1e-3) / 1e9 / peak,
+                         "bytes": "source read once + 8 B per output pixel"},
+            "tuned": cfg}
+
+
+def measure_adjoint2048(dfr, torch, flush, steps):
+    """The differentiation configuration: 2048^2 SIP3 source, bilinear, split, Newton inverse;
+    forward (value + footprint) and the adjoint (gradients of the source pixels and of all 24
+    WCS parameters) of one frame."""
+    c = synth.config3()
+    src = dfr.to_c(dfr.fit_inverse_sip(c["src"][0], 4)[0])
+    tgt = dfr.to_c(c["tgt"])
+    img = torch.from_numpy(c["images"][0]).cuda()
+    g = torch.randn((2048, 2048), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    gs = torch.zeros_like(img)
+    bb = (0, 0, 2048, 2048)
+    npx = 2048 * 2048
+    fwd = lambda: dfr.reproject(img, src, tgt, bbox=bb, order="bilinear", exact_inverse=True)
+    bwd = lambda: dfr.reproject_backward(img, src, tgt, g, bb, "bilinear", "split",
+                                         exact_inverse=True, grad_src=gs)
+    fwd()
+    bwd()
+    t_f = _events_time(fwd, steps, flush)[0]
+    t_b = _events_time(bwd, steps, flush)[0]
+    dfr.device_status()
+    peak = _peaks()[0]
+    return {"workload": "2048^2 SIP3 bilinear, Newton inverse, split: forward, adjoint (source "
+                        "pixels + 24 parameters)",
+            "forward_ms": t_f, "adjoint_ms": t_b, "forward_mpix_s": npx / t_f / 1e3,
+            "adjoint_mpix_s": npx / t_b / 1e3,
+            "forward_frac_hbm": 12 * npx / (t_f * 1e-3) / 1e9 / peak,
+            "adjoint_frac_hbm": 12 * npx / (t_b * 1e-3) / 1e9 / peak,
+            "bytes_per_pixel": 12}
 
 
 def run_oracle(args):
@@ -671,6 +807,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the batch and adjoint keys of the bench line")
     ap.add_argument("--workload", default="sip3_4096",
                     choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "coadd32",
                              "tsip4096", "lanczos4096", "bspline4096", "all", "oracle"],

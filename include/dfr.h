@@ -181,6 +181,23 @@ int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
 int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                                 int32_t order, uint32_t flags, void* stream);
 
+/* Launch configurations the library last chose (a report for benchmarks and tuning; the paper
+ * has no counterpart). out[5], host memory: [0] the tile height (rows of target pixels per
+ * staged source box, 8, 16 or 32; 0: no staging) of the last split-precision dfr_reproject;
+ * [1..4] of the last dfr_reproject_batch: form (1: a CUDA graph of single-frame kernels in
+ * parallel chains, 0: one persistent kernel), chains or CTAs per SM, TMA staging (0/1), tile
+ * height. Process-wide (the last call on any device or thread). DFR_ERR_INVALID_ARG if out is
+ * NULL. */
+int dfr_last_launch_config(int32_t* out);
+
+/* Measured throughput of the arithmetic pipes on the current device (the denominators of the
+ * all-FP64 path's roofline; the paper has no counterpart). out[4], host memory, operations
+ * per second: [0] FP64 flops by fused multiply-add (2 per DFMA), [1] FP32 flops by scalar
+ * FFMA, [2] FP32 flops by packed FP32x2 FMA (4 per instruction), [3] special-function results
+ * per second (sin.approx.f32). Each from the best of three launches of a kernel of 8 independent
+ * chains per thread filling every SM; synchronises `stream`; about 0.1 s. */
+int dfr_measure_pipe_peaks(double* out, void* stream);
+
 /* Cubic B-spline prefilter (the interpolation coefficients of DFR_BSPLINE3): per row, then per
  * column, the recursive filter with pole z = sqrt(3) - 2 and gain 6 (Unser, Aldroubi & Eden,
  * 1991; the causal start summed over a mirrored horizon, the anticausal start in closed form),

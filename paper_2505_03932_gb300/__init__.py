@@ -19,7 +19,8 @@ import numpy as np
 __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
-    "coadd", "coadd_normalize", "reproject_host", "calculate_reprojection",
+    "coadd", "coadd_normalize", "reproject_host", "calculate_reprojection", "last_launch_config",
+    "measure_pipe_peaks",
     "Reproject", "device_status", "bspline_prefilter", "NEAREST", "BILINEAR", "BICUBIC",
     "LANCZOS3", "BSPLINE3", "FP64", "SPLIT",
     "EXACT_INVERSE", "NO_TMA", "NAN_MASK",
@@ -107,6 +108,8 @@ def lib():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
+        L.dfr_last_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int32)]
+        L.dfr_measure_pipe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
         L.dfr_device_status.argtypes = [ctypes.c_void_p]
         _LIB = L
     return _LIB
@@ -180,6 +183,26 @@ def num_params(src) -> int:
     if n < 0:
         _check(n)
     return n
+
+
+def last_launch_config():
+    """The launch configurations the library last chose (dfr_last_launch_config): a dict with
+    the single-frame tile height and the last batch's form, chains / CTAs per SM, TMA, tile
+    height."""
+    v = (ctypes.c_int32 * 5)()
+    _check(lib().dfr_last_launch_config(v))
+    return {"single_tile_h": int(v[0]),
+            "batch": {"form": "graph" if v[1] == 1 else "persistent", "k": int(v[2]),
+                      "tma": bool(v[3]), "tile_h": int(v[4])}}
+
+
+def measure_pipe_peaks(stream=None):
+    """Measured pipe throughput of the current device (dfr_measure_pipe_peaks), in operations per
+    second: FP64 FMA flops, FP32 FMA flops (scalar, packed FP32x2), special-function results."""
+    v = (ctypes.c_double * 4)()
+    _check(lib().dfr_measure_pipe_peaks(v, _stream_ptr(stream)))
+    return {"fp64_fma_flops": v[0], "fp32_fma_flops": v[1], "fp32x2_fma_flops": v[2],
+            "mufu_per_s": v[3]}
 
 
 def device_status(stream=None):

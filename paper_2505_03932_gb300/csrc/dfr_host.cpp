@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cctype>
 #include <cmath>
 #include <cstdarg>
@@ -769,6 +770,10 @@ cudaError_t launch_single(const FwdPlan& P, cudaStream_t s) {
   return launch_forward(Pk, L, grid, forward_threads_default(), smem_for(P), s);
 }
 
+// Launch configurations last used (dfr_last_launch_config): single-frame tile height; batch
+// form, chains or CTAs per SM, TMA, tile height.
+std::atomic<int> g_last_cfg[5];
+
 bool autotune_on() {
   const char* e = std::getenv("DFR_AUTOTUNE");
   return !(e && e[0] == '0');
@@ -1159,12 +1164,19 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
                        out_h, order, flags, coords_out, -1, P, th);
   if (rc != DFR_OK) return rc;
   if (out_w == 0 || out_h == 0) return DFR_OK;
+  if (flags & DFR_SPLIT) g_last_cfg[0].store(P.use_tma ? th : 0);
   cudaError_t e = launch_single(P, s);
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject launch");
   if ((flags & DFR_SPLIT) && coords_out) {
     e = launch_split_coords(P, s);
     if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject coordinate launch");
   }
+  return DFR_OK;
+}
+
+int dfr_last_launch_config(int32_t* out) {
+  if (!out) return fail(DFR_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < 5; ++k) out[k] = g_last_cfg[k].load();
   return DFR_OK;
 }
 
@@ -1475,6 +1487,10 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   }
   int floats = 0;
   for (int f = 0; f < n; ++f) floats = std::max(floats, box_floats(c.h_plans[f]));
+  g_last_cfg[1].store(std::get<0>(cfg));
+  g_last_cfg[2].store(std::get<1>(cfg));
+  g_last_cfg[3].store(std::get<2>(cfg));
+  g_last_cfg[4].store(std::get<3>(cfg));
   if (std::get<0>(cfg) == 1) {
     // kernel parameters are copied into the graph: nothing host-side to protect afterwards
     return launch_fan(c, n, std::get<1>(cfg), s);
