@@ -14,10 +14,12 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdfr.so")
 OBJ = os.path.join(HERE, "_build")
-SOURCES = ["dfr_fwd.cu", "dfr_fwd_single_t16.cu", "dfr_fwd_single_t8.cu", "dfr_fwd_single_t32.cu",
-           "dfr_fwd_batch_t16.cu", "dfr_fwd_batch_t8.cu", "dfr_fwd_batch_t32.cu", "dfr_bwd.cu",
-           "dfr_bwd_tile.cu", "dfr_coadd.cu", "dfr_bspline.cu", "dfr_host.cpp", "dfr_static.cu",
-           "dfr_peaks.cu"]
+SOURCES = ["dfr_fwd_single_t16.cu", "dfr_fwd_single_sw_t16.cu", "dfr_fwd_batch_t16.cu",
+           "dfr_fwd_batch_sw_t16.cu", "dfr_fwd_single_t32.cu", "dfr_fwd_single_sw_t32.cu",
+           "dfr_fwd_batch_t32.cu", "dfr_fwd_batch_sw_t32.cu", "dfr_fwd_single_t8.cu",
+           "dfr_fwd_single_sw_t8.cu", "dfr_fwd_batch_t8.cu", "dfr_fwd_batch_sw_t8.cu",
+           "dfr_fwd.cu", "dfr_bwd.cu", "dfr_bwd_tile.cu", "dfr_coadd.cu", "dfr_bspline.cu",
+           "dfr_host.cpp", "dfr_static.cu", "dfr_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

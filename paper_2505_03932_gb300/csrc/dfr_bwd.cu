@@ -265,7 +265,8 @@ static const void* bwd_for_order(int fd) {
 // degree <= 5 (its per-lane accumulators: 6 + 2 * 20 registers); the per-pixel kernel serves
 // the rest (FP64 path, degree 9, sources without a tensor map).
 static bool staged(const FwdPlan& p0, int fd) {
-  return (p0.flags & DFR_SPLIT) && p0.use_tma && fd <= 5 && p0.order != DFR_LANCZOS3;
+  return (p0.flags & DFR_SPLIT) && p0.use_tma && !p0.stage_sw && fd <= 5 &&
+         p0.order != DFR_LANCZOS3;
 }
 
 static const void* bwd_kernel_for(const FwdPlan& p0, int fd) {

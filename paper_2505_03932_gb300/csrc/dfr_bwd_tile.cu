@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __gr
       const int cox = (cell % P.cells_x) * kCellW, coy = (cell / P.cells_x) * kCellH;
       Anchor a;
       const ColCubic cc = cell_fit<false, true>(P, Q, cox, coy, lane, a);
-      Q.use_tma = P.use_tma != 0 && !dead;
+      Q.use_tma = P.use_tma != 0 && !P.stage_sw && !dead;
       float acc[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[q] = 0.f;

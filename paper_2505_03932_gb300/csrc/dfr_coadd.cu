@@ -12,7 +12,7 @@ namespace dfr {
 template <int ORDER>
 static const void* coadd_for_order(bool split) {
   if (!split) return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, true>);
-  return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, true, kDefaultTileH>);
+  return reinterpret_cast<const void*>(&fwd_split_kernel<ORDER, false, true, kDefaultTileH, true>);
 }
 
 // Single-frame accumulating kernel for a plan (frames of a co-add are launched one after

@@ -50,8 +50,15 @@ static const void* fp64_for_order() {
   return reinterpret_cast<const void*>(&fwd_fp64_kernel<ORDER, kFp64Threads, false>);
 }
 
-// Split kernel of a launch form and tile height (8, 16 or 32 rows), from its instantiation unit.
-static const void* split_for(int order, bool batch, int th) {
+// Split kernel of a launch form, tile height (8, 16 or 32 rows) and staging (sw: a plan of the
+// launch stages its boxes by asynchronous copies), from its instantiation unit.
+static const void* split_for(int order, bool batch, int th, bool sw) {
+  if (sw) {
+    if (batch) return th == 8 ? split_batch_sw_t8(order) : th == 32 ? split_batch_sw_t32(order)
+                                                                    : split_batch_sw_t16(order);
+    return th == 8 ? split_single_sw_t8(order) : th == 32 ? split_single_sw_t32(order)
+                                                          : split_single_sw_t16(order);
+  }
   if (batch) return th == 8 ? split_batch_t8(order) : th == 32 ? split_batch_t32(order)
                                                                : split_batch_t16(order);
   return th == 8 ? split_single_t8(order) : th == 32 ? split_single_t32(order)
@@ -62,7 +69,7 @@ static const void* split_for(int order, bool batch, int th) {
 // launch and taken from p0; batch launches read their plans from a table.
 static const void* forward_kernel_for(const FwdPlan& p0, bool batch) {
   if (p0.flags & kFlagAccumulate) return batch ? nullptr : coadd_kernel(p0);
-  if (p0.flags & DFR_SPLIT) return split_for(p0.order, batch, p0.th);
+  if (p0.flags & DFR_SPLIT) return split_for(p0.order, batch, p0.th, p0.stage_sw != 0);
   switch (p0.order) {
     case DFR_NEAREST: return fp64_for_order<DFR_NEAREST>();
     case DFR_BILINEAR: return fp64_for_order<DFR_BILINEAR>();

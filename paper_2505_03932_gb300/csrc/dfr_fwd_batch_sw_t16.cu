@@ -1,0 +1,5 @@
+// Batched (frame table) split forward kernels, tile height 16, with
+// asynchronous-copy box staging (see dfr_fwd_inst.cuh).
+#include "dfr_fwd_inst.cuh"
+
+DFR_SPLIT_SET(split_batch_sw_t16, true, 16, true)

@@ -542,6 +542,20 @@ __device__ __forceinline__ int frame_of(const FwdLaunch& L, int t) {
   return lo;
 }
 
+// The same frame, found by one warp: a 32-way search over the prefix table, each step one
+// coalesced load per lane and a ballot (one step for up to 32 frames, two up to 1024).
+__device__ __forceinline__ int frame_of_warp(const FwdLaunch& L, int t, int lane) {
+  int lo = 0, n = L.nframes;  // tile_start[lo] <= t; the frame is in [lo, lo + n)
+  while (n > 1) {
+    const int step = (n + 31) >> 5;
+    const bool le = lane * step < n && __ldg(&L.tile_start[lo + lane * step]) <= t;
+    const int k = 31 - __clz(int(__ballot_sync(0xffffffffu, le)));  // lane 0 always holds
+    lo += k * step;
+    n = min(step, n - k * step);
+  }
+  return lo;
+}
+
 template <int ORDER, int NT, bool ACC>
 __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ FwdPlan p0,
                                                       const FwdLaunch L) {
@@ -561,16 +575,18 @@ __global__ void __launch_bounds__(NT) fwd_fp64_kernel(const __grid_constant__ Fw
   }
 }
 
-// BATCH: frame plans in global memory (persistent launch over a frame table, cells taken from
-// an atomic counter); otherwise one frame whose plan is the kernel parameter, one cell per CTA
-// (from L.unit_begin).
+// BATCH: frame plans in global memory (a frame table: the cells of all frames in one index
+// space, frame by frame, found from the prefix table); otherwise one frame whose plan is the
+// kernel parameter, cells [unit_begin, unit_begin + grid) (a band of the box, or all of it).
+// Either way one cell per CTA: the hardware scheduler balances the launch; the cells of its
+// last partial wave may be split into units of fewer tiles (split_from, split_k).
 //
-// A CTA is one warp and owns one 32 x 64 cell at a time: the warp fits the cell's column
-// cubics (cell_fit), then the cell's rows go by in tiles of TH rows, the next tile's source
-// box requested (TMA, double buffered) before the current one is gathered. After a bounded
-// wait gives up, the warp issues no more box loads and gathers from global memory; before
-// exiting it waits (bounded) for any copy still in flight into its buffers.
-template <int ORDER, bool BATCH, bool ACC, int TH>
+// A CTA is one warp and owns one 32 x 64 cell: the warp fits the cell's column cubics
+// (cell_fit), then the cell's rows go by in tiles of TH rows, the next tile's source box
+// requested (TMA or asynchronous copies, double buffered) before the current one is gathered.
+// After a bounded wait gives up, the warp issues no more box loads and gathers from global
+// memory; before exiting it waits (bounded) for any copy still in flight into its buffers.
+template <int ORDER, bool BATCH, bool ACC, int TH, bool SW>
 __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_kernel(
     const __grid_constant__ FwdPlan p0, const FwdLaunch L) {
   static_assert(kCellH % TH == 0 && TH % 2 == 0, "tile height must divide the cell");
@@ -591,28 +607,22 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
   bool dead = false;     // a wait gave up: no more copies from this warp
   constexpr bool batch = BATCH;
   constexpr int NT = kCellH / TH;
-  // cells; a single-frame launch may cover cells [unit_begin, unit_begin + grid) only (bands).
-  // Single-frame launches may split the cells of their last partial wave (from cell
-  // split_from on) into split_k work units of NT / split_k tiles each.
+  // the cell of this CTA; cells from split_from on are split into split_k units of NT /
+  // split_k tiles each
   const int total = batch ? L.tile_start[L.nframes] : L.total_tiles;
-  int id = blockIdx.x + L.unit_begin;
+  int id = blockIdx.x + (batch ? 0 : L.unit_begin);
   int t0 = 0, t1 = NT;
-  if (!batch && L.split_k > 1 && id >= L.split_from) {
+  if (L.split_k > 1 && id >= L.split_from) {
     const int u = id - L.split_from, part = u % L.split_k;
     id = L.split_from + u / L.split_k;
     t0 = part * (NT / L.split_k);
     t1 = t0 + NT / L.split_k;
   }
-  if (batch) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(L.counter, 1);
-    id = __shfl_sync(0xffffffffu, t, 0);
-  }
-  while (id < total) {
+  if (id < total) {
     int f = 0, cell = id;
     if (batch) {
-      f = frame_of(L, cell);
-      cell -= L.tile_start[f];
+      f = frame_of_warp(L, cell, lane);
+      cell -= __ldg(&L.tile_start[f]);
     }
     const FwdPlan& P = batch ? L.plans[f] : p0;
     HP Q;
@@ -626,23 +636,32 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
     const bool fast_cell = !Q.mask && cc.valid &&
                            __all_sync(0xffffffffu, cubic_bow(cc, TH) <= 0.5f) &&
                            cox + kCellW <= Q.w;
-    TileBox cur = tile_box<ORDER>(P, Q, a, cc, cox, coy + t0 * TH, t0 * TH, TH, lane,
+    TileBox cur = tile_box<ORDER, SW>(P, Q, a, cc, cox, coy + t0 * TH, t0 * TH, TH, lane,
                                   box + (t0 & 1) * L.box_floats, &bar[t0 & 1], batch, true,
                                   L.tx_extra);
-    if (cur.use_box) pending |= 1u << (t0 & 1);
+    const bool sw = SW && Q.stage_sw;
+    if (cur.use_box && !sw) pending |= 1u << (t0 & 1);
     prefetch_sums<ACC>(Q, cox, coy + t0 * TH, TH, lane);
     for (int t = t0; t < t1; ++t) {
       const int b = t & 1;
       TileBox nxt;
       nxt.use_box = false;
       if (t + 1 < t1) {
-        nxt = tile_box<ORDER>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
+        nxt = tile_box<ORDER, SW>(P, Q, a, cc, cox, coy + (t + 1) * TH, (t + 1) * TH, TH, lane,
                               box + (b ^ 1) * L.box_floats, &bar[b ^ 1], batch, true, L.tx_extra);
-        if (nxt.use_box) pending |= 1u << (b ^ 1);
+        if (nxt.use_box && !sw) pending |= 1u << (b ^ 1);
         prefetch_sums<ACC>(Q, cox, coy + (t + 1) * TH, TH, lane);
       }
       uint32_t tok = 0;
-      if (cur.use_box) {
+      if (cur.use_box && sw) {
+        // this tile's copies (all but the newest group when the next box is on its way)
+        if (nxt.use_box)
+          cp_async_wait<1>();
+        else
+          cp_async_wait<0>();
+        __syncwarp();
+        tok = box_token();
+      } else if (cur.use_box) {
         if (mbar_wait(&bar[b], (phase >> b) & 1u)) {
           phase ^= 1u << b;
           pending &= ~(1u << b);
@@ -664,15 +683,12 @@ __global__ void __launch_bounds__(kFwdWarps * 32, kSplitMinBlocks) fwd_split_ker
         tile_rows<ORDER, ACC>(P, Q, a, cc, gx, oy, t * TH, TH, bt, cur);
       cur = nxt;
     }
-    if (!batch) break;
-    int t = 0;
-    if (lane == 0) t = atomicAdd(L.counter, 1);
-    id = __shfl_sync(0xffffffffu, t, 0);
   }
   // copies this warp issued and never saw complete (after a wait gave up) must land before
   // the CTA's shared memory is released
   for (int b = 0; b < 2; ++b)
     if ((pending >> b) & 1u) mbar_wait(&bar[b], (phase >> b) & 1u, false);
+  if (SW) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 }  // namespace dfr

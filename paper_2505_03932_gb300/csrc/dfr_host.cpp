@@ -336,8 +336,9 @@ int smem_for_floats(int floats);
 void set_tile_height(FwdPlan& P, int th) {
   P.th = th;
   P.use_tma = 0;
+  P.stage_sw = 0;
   P.box_w = P.box_h = 0;
-  if (!P.tma_ok) return;
+  if (P.tma_ok < 1) return;  // 0: no staging (DFR_NO_TMA, or nothing to stage)
   const double B = th - 1;
   // the kernels take every lane's first and last row exactly: the margin covers the bow of a
   // column between them (twice the sampled bound), at least 1 px
@@ -351,6 +352,14 @@ void set_tile_height(FwdPlan& P, int th) {
   const int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
   const int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
   if (bw > kBoxW || bh > 256 || smem_for_floats(kBoxW * bh) > 110 * 1024) return;
+  if (P.tma_ok == 2) {  // a source TMA cannot describe: asynchronous per-thread copies
+    P.box_w = kBoxW;
+    P.box_h = bh;
+    P.use_tma = 1;
+    P.stage_sw = 1;
+    return;
+  }
+  P.stage_sw = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return;
   cuuint64_t gdim[2] = {cuuint64_t(P.W), cuuint64_t(P.H)};
@@ -516,8 +525,9 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   P.th = th;
   if ((flags & DFR_SPLIT) && !(flags & DFR_NO_TMA) && w > 0 && h > 0) {
     size_box(P);
+    // staging: 1 = TMA (16-byte aligned base and pitch), 2 = per-thread asynchronous copies
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 16 == 0) && ((pitch * 4) % 16 == 0);
-    P.tma_ok = aligned && get_encode() != nullptr;
+    P.tma_ok = (aligned && get_encode() != nullptr) ? 1 : 2;
     set_tile_height(P, th);
   }
   return DFR_OK;
@@ -717,16 +727,16 @@ uint32_t fault_tx_extra() {
 // frame fills less than a wave) are split into k units of fewer tiles (k a power of two up to
 // the tiles per cell, the smallest that fills a wave), so that the launch does not end on a
 // thin wave of long CTAs. Returns the grid; sets split_from and split_k.
-int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k) {
+int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k,
+               bool batch = false, int smem = -1) {
   static std::mutex mu;
-  static std::map<std::tuple<int, const void*, int>, int> occ;
+  static std::map<std::tuple<int, const void*, int, bool>, int> occ;
   split_from = cells;
   split_k = 1;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cells;
-  const int smem = smem_for(P);
-  const void* k = forward_kernel(P);
-  const auto key = std::make_tuple(dev, k, smem);
+  if (smem < 0) smem = smem_for(P);
+  const auto key = std::make_tuple(dev, forward_kernel(P), smem, batch);
   int n = 0;
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -734,7 +744,7 @@ int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_
     if (it != occ.end()) n = it->second;
   }
   if (n == 0) {
-    n = forward_max_blocks_per_sm(P, kFwdWarps * 32, smem, false);
+    n = forward_max_blocks_per_sm(P, kFwdWarps * 32, smem, batch);
     std::lock_guard<std::mutex> lock(mu);
     occ[key] = n;
   }
@@ -1198,7 +1208,10 @@ int dfr_device_status(void* stream) {
   e = read_and_clear_status_coadd(&d, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
   for (auto rd : {split_single_t8_status, split_single_t16_status, split_single_t32_status,
-                  split_batch_t8_status, split_batch_t16_status, split_batch_t32_status}) {
+                  split_batch_t8_status, split_batch_t16_status, split_batch_t32_status,
+                  split_single_sw_t8_status, split_single_sw_t16_status,
+                  split_single_sw_t32_status, split_batch_sw_t8_status,
+                  split_batch_sw_t16_status, split_batch_sw_t32_status}) {
     int32_t u = 0;
     e = rd(&u, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "dfr_device_status");
@@ -1224,9 +1237,25 @@ bool autotune_enabled() {
 int dfr::batch_units(const FwdPlan& P) {
   return (P.flags & DFR_SPLIT) ? P.cells_x * P.cells_y : P.tiles_x * P.tiles_y;
 }
+// The plan that selects a batch launch's kernel: frame 0's, marked for asynchronous-copy
+// staging when any frame stages its boxes that way.
+FwdPlan dfr::batch_head(const FwdPlan* plans, int n) {
+  FwdPlan h = plans[0];
+  h.stage_sw = 0;
+  for (int f = 0; f < n; ++f)
+    if (plans[f].use_tma && plans[f].stage_sw) h.stage_sw = 1;
+  return h;
+}
+
+// Grid of a split launch over `cells` cells (one CTA per cell, the last partial wave split).
+int dfr::split_grid(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k,
+                    bool batch, int smem) {
+  return tail_split(P, cells, split_from, split_k, batch, smem);
+}
 namespace {
 
-// Upload the frame table, zero the work counter and launch the persistent kernel.
+// Upload the frame table, zero the work counter and launch the batch kernel: for the split path
+// one CTA per cell of the table, for the FP64 path a persistent grid of `grid` CTAs.
 cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int floats, cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaMemcpyAsync(c.d_plans, c.h_plans, size_t(n) * sizeof(FwdPlan),
@@ -1242,7 +1271,11 @@ cudaError_t enqueue_batch(DeviceCtx& c, int n, int grid, int floats, cudaStream_
   L.nframes = n;
   L.counter = c.d_counter;
   L.box_floats = floats;
-  return launch_forward(c.h_plans[0], L, grid, forward_threads_default(),
+  const FwdPlan head = batch_head(c.h_plans, n);
+  if (head.flags & DFR_SPLIT)  // one CTA per cell of the table (last wave split)
+    grid = tail_split(head, c.h_starts[n], L.split_from, L.split_k, true,
+                      smem_for_floats(floats));
+  return launch_forward(head, L, grid, forward_threads_default(),
                         smem_for_floats(floats), s);
 }
 
@@ -1370,6 +1403,10 @@ int launch_fan(DeviceCtx& c, int n, int lanes, cudaStream_t s) {
 // height).
 std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStream_t s) {
   const int threads = forward_threads_default();
+  // DFR_BATCH_FORM=graph or =table limits the search to one launch form
+  const char* form = std::getenv("DFR_BATCH_FORM");
+  const bool try_graph = !(form && std::strcmp(form, "table") == 0);
+  const bool try_table = !(form && std::strcmp(form, "graph") == 0);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1387,19 +1424,22 @@ std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStre
     }
     const std::vector<FwdPlan> base(c.h_plans, c.h_plans + n);
     const int smem = smem_for_floats(floats);
-    const int maxb = forward_max_blocks_per_sm(c.h_plans[0], threads, smem);
-    // CTAs per SM: one-warp CTAs for the split kernel, 256-thread CTAs for the FP64 kernel
-    const std::vector<int> ks = split ? std::vector<int>{6, 10, 16} : std::vector<int>{1, 2, 4, 8};
+    const int maxb = forward_max_blocks_per_sm(batch_head(c.h_plans, n), threads, smem);
+    // FP64: the persistent kernel at several CTAs per SM; split: the grid over every cell of
+    // the table (its size follows from the cells)
+    const std::vector<int> ks = split ? std::vector<int>{1} : std::vector<int>{1, 2, 4, 8};
     std::vector<std::pair<int, int>> cand;
     for (int k : ks)
       if (k <= maxb) cand.push_back({k, smem > 0 ? 1 : 0});
     if (smem > 0 && th == kDefaultTileH) {
-      const int maxb0 = forward_max_blocks_per_sm(c.h_plans[0], threads, 0);
+      const int maxb0 = forward_max_blocks_per_sm(batch_head(c.h_plans, n), threads, 0);
       for (int k : ks)
         if (k <= maxb0) cand.push_back({k, 0});
     }
+    if (!try_table) cand.clear();
     for (int lanes : {1, 2, 4, 64}) {
       // graphs of single-frame kernels in `lanes` parallel chains
+      if (!try_graph) break;
       if (lanes > 1 && lanes / 2 >= n) break;
       bool ok = true;
       for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -1499,7 +1539,9 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
     for (int f = 0; f < n; ++f) c.h_plans[f].use_tma = 0;
     floats = 0;
   }
-  const int grid = std::max(1, std::min(int(total), c.sms * std::get<1>(cfg)));
+  // FP64: persistent grid; split: one CTA per cell, so the cell count is part of the key
+  const int grid = (flags & DFR_SPLIT) ? int(total)
+                                       : std::max(1, std::min(int(total), c.sms * std::get<1>(cfg)));
   GraphKey gk{n, order, int(flags), ideg, grid, floats, std::get<3>(cfg)};
   auto g = c.graphs.find(gk);
   if (g == c.graphs.end()) {

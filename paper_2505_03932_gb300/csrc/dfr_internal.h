@@ -60,10 +60,13 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   const float* img;
   int64_t pitch;
   int32_t W, H;
-  int32_t use_tma, box_w, box_h;
+  int32_t use_tma, box_w, box_h;  // use_tma: source boxes staged in shared memory (by TMA,
+                             // or, with stage_sw, by per-thread asynchronous copies)
+  int32_t stage_sw;          // boxes staged by cp.async (a source whose row pitch TMA cannot
+                             // describe: not a multiple of 16 bytes, or a base not 16-aligned)
   int32_t box_margin;        // px added around a tile's corner extent (covers map curvature)
   int32_t th;                // tile height (rows) the box and its tensor map are sized for
-  int32_t tma_ok;            // the source allows TMA (16-byte aligned base and pitch)
+  int32_t tma_ok;            // box staging the source allows: 1 TMA, 2 asynchronous copies, 0 none
   float jac[4];              // host bounds of |dx/dX|, |dx/dY|, |dy/dX|, |dy/dY| (box sizing)
   float curv[3];             // host bounds of the map's second derivatives (xx, xy, yy)
   int32_t identity;          // source and target WCS are bitwise equal
@@ -147,13 +150,24 @@ enum : int32_t { kStatusTimeout = 1, kStatusCheck = 2 };
 cudaError_t launch_forward(const FwdPlan& p0, const FwdLaunch& L, int grid, int threads,
                            int smem_bytes, cudaStream_t s);
 const void* forward_kernel(const FwdPlan& p0);
-// split kernels by launch form and tile height (dfr_fwd_{single,batch}_t{8,16,32}.cu)
-const void* split_single_t8(int order);
-const void* split_single_t16(int order);
-const void* split_single_t32(int order);
-const void* split_batch_t8(int order);
-const void* split_batch_t16(int order);
-const void* split_batch_t32(int order);
+// split kernels by launch form, staging and tile height
+// (dfr_fwd_{single,batch}[_sw]_t{8,16,32}.cu) and their status readers
+#define DFR_SPLIT_DECL(NAME)    \
+  const void* NAME(int order); \
+  cudaError_t NAME##_status(int32_t* out, cudaStream_t s);
+DFR_SPLIT_DECL(split_single_t8)
+DFR_SPLIT_DECL(split_single_t16)
+DFR_SPLIT_DECL(split_single_t32)
+DFR_SPLIT_DECL(split_batch_t8)
+DFR_SPLIT_DECL(split_batch_t16)
+DFR_SPLIT_DECL(split_batch_t32)
+DFR_SPLIT_DECL(split_single_sw_t8)
+DFR_SPLIT_DECL(split_single_sw_t16)
+DFR_SPLIT_DECL(split_single_sw_t32)
+DFR_SPLIT_DECL(split_batch_sw_t8)
+DFR_SPLIT_DECL(split_batch_sw_t16)
+DFR_SPLIT_DECL(split_batch_sw_t32)
+#undef DFR_SPLIT_DECL
 cudaError_t launch_split_coords(const FwdPlan& p0, cudaStream_t s);
 int forward_max_blocks_per_sm(const FwdPlan& p0, int threads, int smem_bytes, bool batch = true);
 int forward_threads_default();
@@ -161,12 +175,6 @@ cudaError_t read_and_clear_status_fwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_bwd_tile(int32_t* out, cudaStream_t s);
 cudaError_t read_and_clear_status_coadd(int32_t* out, cudaStream_t s);
-cudaError_t split_single_t8_status(int32_t* out, cudaStream_t s);
-cudaError_t split_single_t16_status(int32_t* out, cudaStream_t s);
-cudaError_t split_single_t32_status(int32_t* out, cudaStream_t s);
-cudaError_t split_batch_t8_status(int32_t* out, cudaStream_t s);
-cudaError_t split_batch_t16_status(int32_t* out, cudaStream_t s);
-cudaError_t split_batch_t32_status(int32_t* out, cudaStream_t s);
 cudaError_t launch_backward(const FwdPlan& p0, const BwdExtra& B, cudaStream_t s);
 int backward_num_padded(int fd);
 int backward_max_blocks_per_sm(const FwdPlan& p0, int fd, int smem_bytes);
@@ -189,6 +197,9 @@ int plan_for_frame(const dfr_frame& fr, const dfr_wcs* tgt, int32_t order, uint3
 int inverse_degree_for(const dfr_frame* frames, int n);
 int plan_box_floats(const FwdPlan& P);
 int batch_units(const FwdPlan& P);
+FwdPlan batch_head(const FwdPlan* plans, int n);
+int split_grid(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k, bool batch,
+               int smem);
 int plan_smem_bytes(int floats);
 int report_error(int code, const char* msg);
 int report_cuda_error(cudaError_t e, const char* where);

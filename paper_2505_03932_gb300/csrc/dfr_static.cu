@@ -99,9 +99,15 @@ extern "C" int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n,
   L.box_floats = floats;
   const int smem = plan_smem_bytes(floats);
   const int threads = forward_threads_default();
-  const int per_sm = forward_max_blocks_per_sm(g_host_plans[0], threads, smem);
-  const int grid = std::max(1, std::min(int(total), g_sms[dev] * per_sm));
-  e = launch_forward(g_host_plans[0], L, grid, threads, smem, s);
+  const FwdPlan head = batch_head(g_host_plans, n);
+  int grid;
+  if (head.flags & DFR_SPLIT) {
+    grid = split_grid(head, int(total), L.split_from, L.split_k, true, smem);
+  } else {
+    const int per_sm = forward_max_blocks_per_sm(head, threads, smem);
+    grid = std::max(1, std::min(int(total), g_sms[dev] * per_sm));
+  }
+  e = launch_forward(head, L, grid, threads, smem, s);
   if (e != cudaSuccess) return report_cuda_error(e, "dfr_reproject_batch_noalloc launch");
   return DFR_OK;
 }

@@ -15,7 +15,7 @@ struct HotPlan {
   static constexpr int NC = (IDEG > 0 && PAIRS) ? poly_ncoef(IDEG) : 1;
   float2 cab[NC];
   int32_t W, H, w, h, x0, y0, box_w, box_h;
-  bool identity, tsip, newton, use_tma, mask;
+  bool identity, tsip, newton, use_tma, mask, stage_sw;
   int64_t out_pitch;
   float* out;
   float* fp;
@@ -40,6 +40,7 @@ __device__ __forceinline__ void load_hot(const FwdPlan& P, HotPlan<IDEG, PAIRS>&
   Q.tsip = P.tsip_deg > 0;
   Q.newton = plan_newton(P);
   Q.use_tma = P.use_tma != 0;
+  Q.stage_sw = P.stage_sw != 0;
   Q.mask = (P.flags & DFR_NAN_MASK) != 0;
   Q.out_pitch = P.out_pitch;
   Q.out = P.out;
@@ -309,7 +310,41 @@ struct TileBox {
   bool empty;        // the widened extent misses the image: nothing in the tile is covered
 };
 
-template <int ORDER>
+// Box staging without TMA (stage_sw plans): every lane copies the columns lane and lane + 32
+// of the kBoxW-wide box, row by row, with 4-byte asynchronous copies (cp.async), zero-filled
+// outside the image like the TMA tile fill, as one commit group per box. The copies land
+// before cp_async_wait (by the lane that issued them) plus a warp barrier.
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src, bool inside) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)),
+               "l"(src), "r"(inside ? 4 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void stage_box_sw(const FwdPlan& P, const HP& Q, float* box, int bx0,
+                                             int by0, int lane) {
+  static_assert(kBoxW == 64, "two columns per lane");
+  for (int j = 0; j < Q.box_h; ++j) {
+    const int gy = by0 + j;
+    const bool iny = unsigned(gy) < unsigned(Q.H);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h, gx = bx0 + i;
+      const bool in = iny && unsigned(gx) < unsigned(Q.W);
+      // (an address inside the image even where nothing is read)
+      cp_async_f32(box + j * kBoxW + i, P.img + (in ? int64_t(gy) * P.pitch + gx : 0), in);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait for this lane's copies but the newest `keep` commit groups (0 or 1).
+template <int KEEP>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(KEEP) : "memory");
+}
+
+// SW: the kernel may meet stage_sw plans (the asynchronous-copy staging is compiled in).
+template <int ORDER, bool SW = false>
 __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HP& Q, const Anchor& a,
                                             const ColCubic& cc, int ox, int oy, int r0,
                                             int nrows, int lane, float* box, uint64_t* bar,
@@ -362,7 +397,9 @@ __device__ __forceinline__ TileBox tile_box(const FwdPlan& P, const HP& Q, const
   tb.use_box = x_hi - tb.bx0 <= Q.box_w && y_hi - tb.by0 <= Q.box_h;
   if (tb.use_box && load) {  // (load = false: the box geometry only, nothing is copied)
     __syncwarp();  // every lane is done reading this buffer's previous tile
-    if (lane == 0) {
+    if (SW && Q.stage_sw) {
+      stage_box_sw(P, Q, box, tb.bx0, tb.by0, lane);
+    } else if (lane == 0) {
       fence_proxy_async();
       if (map_in_gmem) fence_tensormap_acquire(&P.tmap);
       mbar_expect_tx(bar, uint32_t(Q.box_w) * uint32_t(Q.box_h) * 4u + tx_extra);
