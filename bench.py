@@ -251,7 +251,9 @@ def run_reference(args, rank, world):
         return
     pool = OraclePool()
     try:
-        per_core = 250_000  # about 0.25 s of each core per step
+        # at most about 0.25 s of each core per step, and about 10 s of each core over all
+        # the timed steps (a long timed run takes smaller samples per step)
+        per_core = int(min(250_000, max(2_000, 10_000_000 // max(1, args.steps))))
         for k in range(args.warmup):
             pool.seconds(per_core // 4, seed=1 + k)
         secs = [pool.seconds(per_core, seed=100 + k) for k in range(args.steps)]
@@ -428,13 +430,15 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0 and not args.no_extra:
         extra["batch64"] = measure_batch64(dfr, torch, flush, max(3, min(args.steps, 10)))
         extra["adjoint2048"] = measure_adjoint2048(dfr, torch, flush, max(3, min(args.steps, 10)))
+        extra["stack32"] = measure_stack32(dfr, torch, flush, max(3, min(args.steps, 6)))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "ms_per_step_median": float(np.median(times)),
-            "ms_steps": [round(float(t), 4) for t in times],
+            "ms_steps_first": [round(float(t), 4) for t in times[:16]],
+            "ms_steps_p10_p90": [float(np.percentile(times, 10)), float(np.percentile(times, 90))],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "split", "output_mpix": npix / 1e6,
@@ -557,6 +561,61 @@ def measure_adjoint2048(dfr, torch, flush, steps):
             "bytes_per_pixel": 12}
 
 
+def measure_stack32(dfr, torch, flush, steps):
+    """The stack configuration: 32 exposures of 6000x4000 (SIP5, AP/BP 6) onto one 12000x8000
+    target, bicubic, split precision: the batched forward (value + footprint, one launch form
+    tuned on the first call) and, as the second pass, the batched adjoint (source-pixel and
+    parameter gradients of all 32 frames in one dfr_reproject_backward_batch call) against 32
+    separate dfr_reproject_backward calls."""
+    c = synth.config4()
+    tgt = dfr.to_c(c["tgt"])
+    srcs = [dfr.to_c(dfr.fit_inverse_sip(sw, 6)[0]) for sw in c["src"]]
+    imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
+    src_bytes = sum(i.numel() * 4 for i in imgs)
+    del c
+    bbs = [dfr.target_bbox(sw, tgt) for sw in srcs]
+    outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
+    fps = [torch.empty_like(o) for o in outs]
+    npx = sum(b[2] * b[3] for b in bbs)
+    fwd = lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bicubic", outs=outs, fps=fps)
+    fwd()
+    torch.cuda.synchronize()
+    cfg = dfr.last_launch_config()["batch"]
+    t_f = _events_time(fwd, steps, flush)[0]
+    gen = torch.Generator("cuda").manual_seed(5)
+    go = torch.randn((max(b[3] for b in bbs), max(b[2] for b in bbs)), device="cuda",
+                     generator=gen)
+    gos = [go[:b[3], :b[2]] for b in bbs]
+    gs = [torch.zeros_like(i) for i in imgs]
+    bwd = lambda: dfr.reproject_backward_batch(imgs, srcs, tgt, gos, bbs, "bicubic", "split",
+                                               grad_srcs=gs)
+
+    def bwd_sep():
+        for k in range(len(imgs)):
+            dfr.reproject_backward(imgs[k], srcs[k], tgt, gos[k], bbs[k], "bicubic", "split",
+                                   grad_src=gs[k])
+    bwd()
+    bwd_sep()
+    t_b = _events_time(bwd, max(3, steps // 2), flush)[0]
+    t_s = _events_time(bwd_sep, max(3, steps // 2), flush)[0]
+    dfr.device_status()
+    peak = _peaks()[0]
+    algo = src_bytes + 8 * npx
+    return {"workload": "32 x 6000x4000 SIP5 -> 12000x8000, bicubic, split: batched forward "
+                        "and batched adjoint (source pixels + CRVAL/CD)",
+            "output_mpix": npx / 1e6, "forward_ms": t_f, "forward_mpix_s": npx / t_f / 1e3,
+            "forward_roofline": {"bound": "hbm", "achieved": algo / (t_f * 1e-3) / 1e9,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": algo / (t_f * 1e-3) / 1e9 / peak,
+                                 "bytes": "source read once + 8 B per output pixel"},
+            "forward_tuned": cfg,
+            "adjoint_batch_ms": t_b, "adjoint_separate_ms": t_s,
+            "adjoint_mpix_s": npx / t_b / 1e3,
+            "adjoint_speedup_vs_separate": t_s / t_b,
+            "adjoint_frac_hbm": 12 * npx / (t_b * 1e-3) / 1e9 / peak,
+            "adjoint_bytes_per_pixel": 12}
+
+
 def run_oracle(args):
     """The FP64 CPU oracle, as it stands, in one process on each configuration (no GPU):
     whole frames for the 512^2 and 2048^2 cases, 1M random pixels of the 4096^2 frame, and a
@@ -666,32 +725,7 @@ def run_extra(args):
                     "forward_ms": t_f, "adjoint_ms": t_b,
                     "forward_mpix_s": 4.194304 / t_f * 1e3, "adjoint_mpix_s": 4.194304 / t_b * 1e3})
     if args.workload in ("stack32", "all"):
-        c = synth.config4()
-        tgt = dfr.to_c(c["tgt"])
-        srcs = [dfr.to_c(dfr.fit_inverse_sip(s, 6)[0]) for s in c["src"]]
-        imgs = [torch.from_numpy(i).cuda() for i in c["images"]]
-        bbs = [dfr.target_bbox(s, tgt) for s in srcs]
-        outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
-        fps = [torch.empty_like(o) for o in outs]
-        npx = sum(b[2] * b[3] for b in bbs)
-        fwd = lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order="bicubic", outs=outs, fps=fps)
-        fwd()
-        t_f = _events_time(fwd, max(3, args.steps // 2), flush)[0]
-        gs = [torch.zeros_like(i) for i in imgs]
-        go = torch.randn((max(b[3] for b in bbs), max(b[2] for b in bbs)), device="cuda")
-
-        def bwd():
-            for k in range(32):
-                x0, y0, w, h = bbs[k]
-                dfr.reproject_backward(imgs[k], srcs[k], tgt, go[:h, :w], bbs[k], "bicubic",
-                                       "split", grad_src=gs[k])
-        bwd()
-        t_b = _events_time(bwd, 3, None)[0]
-        out.append({"workload": "32 x 6000x4000 SIP5 -> 12000x8000, bicubic, split batch + adjoint",
-                    "output_mpix": npx / 1e6, "forward_batch_ms": t_f,
-                    "forward_mpix_s": npx / t_f / 1e3, "adjoint_ms": t_b,
-                    "adjoint_mpix_s": npx / t_b / 1e3,
-                    "roofline_frac_hbm": (12 * npx / (t_f * 1e-3)) / 1e9 / _peaks()[0]})
+        out.append(measure_stack32(dfr, torch, flush, max(3, args.steps // 2)))
     if args.workload in ("adjoint6000", "all"):
         # one 6000x4000 SIP5 exposure of the stack configuration: forward, adjoint with the
         # polynomial inverse (CRVAL and CD gradients), adjoint with the Newton inverse (A/B too)
@@ -803,7 +837,8 @@ def run_extra(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=8000,
+                    help="timed steps of the bench line (8000: about 0.55 s of kernel time)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

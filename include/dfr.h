@@ -249,6 +249,32 @@ int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
                            float* grad_src, int64_t gs_pitch,
                            double* grad_params, void* stream);
 
+/* One frame of a batched adjoint: the arguments of one dfr_reproject_backward call. */
+typedef struct dfr_bwd_frame {
+  dfr_wcs      wcs;         /* source WCS                                                   */
+  const float* img;         /* source image, wcs.naxis[1] rows of wcs.naxis[0] floats       */
+  int64_t      pitch;       /* source row stride, elements                                  */
+  const float* grad_out;    /* dL/d(out), h rows of w floats, row stride go_pitch           */
+  int64_t      go_pitch;
+  int32_t      x0, y0, w, h; /* target bounding box of the forward call                     */
+  float*       grad_src;    /* accumulated dL/d(img) (same layout as img, stride gs_pitch);
+                               may be NULL                                                  */
+  int64_t      gs_pitch;
+  double*      grad_params; /* dfr_num_params(&wcs) doubles, may be NULL                    */
+} dfr_bwd_frame;
+
+/* Batched adjoint: the n calls dfr_reproject_backward(frames[f], ...) with one target, order
+ * and flags, issued at once. The frames run side by side on library-owned streams, after the
+ * work enqueued on `stream` before the call and before the work enqueued after it (as if all
+ * ran on `stream`). Each frame's kernels and arguments are those of its single call:
+ * grad_params come out bit for bit equal to the single calls'; grad_src receives the same
+ * terms, added by float atomics whose order (and so the last bits of a sum) may differ, as
+ * between two single calls. Frames may share a grad_src buffer (their terms add up). Errors:
+ * as dfr_reproject_backward, the message naming the frame; nothing is launched when a frame's
+ * arguments are refused. Asynchronous. */
+int dfr_reproject_backward_batch(const dfr_bwd_frame* frames, int32_t n, const dfr_wcs* tgt,
+                                 int32_t order, uint32_t flags, void* stream);
+
 /* Number of doubles dfr_reproject_backward writes to grad_params for this source WCS. */
 int dfr_num_params(const dfr_wcs* src);
 

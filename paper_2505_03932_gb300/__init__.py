@@ -19,6 +19,7 @@ import numpy as np
 __all__ = [
     "DfrError", "lib", "wcs_from_header", "fit_inverse_sip", "target_bbox", "num_params",
     "reproject", "reproject_batch", "reproject_batch_noalloc", "reproject_backward",
+    "reproject_backward_batch",
     "coadd", "coadd_normalize", "reproject_host", "calculate_reprojection", "last_launch_config",
     "measure_pipe_peaks",
     "Reproject", "device_status", "bspline_prefilter", "NEAREST", "BILINEAR", "BICUBIC",
@@ -58,6 +59,14 @@ class DfrFrame(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("footprint", ctypes.c_void_p),
                 ("out_pitch", ctypes.c_int64), ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
                 ("w", ctypes.c_int32), ("h", ctypes.c_int32)]
+
+
+class DfrBwdFrame(ctypes.Structure):
+    _fields_ = [("wcs", DfrWcs), ("img", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("grad_out", ctypes.c_void_p), ("go_pitch", ctypes.c_int64),
+                ("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("grad_src", ctypes.c_void_p), ("gs_pitch", ctypes.c_int64),
+                ("grad_params", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -107,6 +116,9 @@ def lib():
             ctypes.POINTER(DfrWcs), ctypes.POINTER(DfrWcs), ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
+        L.dfr_reproject_backward_batch.argtypes = [ctypes.POINTER(DfrBwdFrame), ctypes.c_int32,
+                                                   ctypes.POINTER(DfrWcs), ctypes.c_int32,
+                                                   ctypes.c_uint32, ctypes.c_void_p]
         L.dfr_num_params.argtypes = [ctypes.POINTER(DfrWcs)]
         L.dfr_last_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int32)]
         L.dfr_measure_pipe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
@@ -497,6 +509,49 @@ def reproject_backward(src_img, src_wcs, tgt_wcs, grad_out, bbox, order="bilinea
         ctypes.c_void_p(gs.data_ptr() if gs is not None else 0), gs.stride(0) if gs is not None else 0,
         ctypes.c_void_p(gp.data_ptr() if gp is not None else 0), _stream_ptr(stream)))
     return gs, gp
+
+
+def reproject_backward_batch(src_imgs, src_wcss, tgt_wcs, grad_outs, bboxes, order="bilinear",
+                             precision="split", exact_inverse=False, grad_srcs=None,
+                             want_src=True, want_params=True, stream=None, tma=True):
+    """Batched adjoint (dfr_reproject_backward_batch): the reproject_backward calls of every
+    frame at once. Returns (list of grad_src or None, list of grad_params or None)."""
+    torch = _torch()
+    n = len(src_imgs)
+    if not (len(src_wcss) == len(grad_outs) == len(bboxes) == n):
+        raise ValueError("src_imgs, src_wcss, grad_outs and bboxes must have the same length")
+    if grad_srcs is not None and len(grad_srcs) != n:
+        raise ValueError("grad_srcs must have one entry per frame")
+    arr = (DfrBwdFrame * max(n, 1))()
+    keep, gss, gps = [], [], []
+    for f in range(n):
+        img = _dev_f32(src_imgs[f], "src_imgs[%d]" % f)
+        _check_image(img, src_wcss[f], "src_imgs[%d]" % f)
+        go = _dev_f32(grad_outs[f], "grad_outs[%d]" % f)
+        x0, y0, w, h = (int(v) for v in bboxes[f])
+        _check_out(go, None, w, h, "grad_outs[%d]" % f)
+        gs = None
+        if want_src:
+            gs = grad_srcs[f] if grad_srcs is not None else torch.zeros_like(img)
+            gs = _dev_f32(gs, "grad_srcs[%d]" % f)
+            _check_image(gs, src_wcss[f], "grad_srcs[%d]" % f)
+        gp = torch.zeros(num_params(src_wcss[f]), dtype=torch.float64, device=img.device) \
+            if want_params else None
+        fr = arr[f]
+        fr.wcs = to_c(src_wcss[f])
+        fr.img, fr.pitch = img.data_ptr(), img.stride(0)
+        fr.grad_out, fr.go_pitch = go.data_ptr(), go.stride(0)
+        fr.x0, fr.y0, fr.w, fr.h = x0, y0, w, h
+        fr.grad_src = gs.data_ptr() if gs is not None else 0
+        fr.gs_pitch = gs.stride(0) if gs is not None else 0
+        fr.grad_params = gp.data_ptr() if gp is not None else 0
+        keep += [img, go]
+        gss.append(gs)
+        gps.append(gp)
+    _check(lib().dfr_reproject_backward_batch(arr, n, ctypes.byref(to_c(tgt_wcs)), _order(order),
+                                              _flags(precision, exact_inverse, tma),
+                                              _stream_ptr(stream)))
+    return gss, gps
 
 
 def _host_ptr(a, name, shape=None):

@@ -21,16 +21,17 @@
 namespace dfr {
 
 constexpr int kBwdThreads = 256;
+constexpr float kBelowOne = 0.99999994f;  // the largest float below 1 (1 - 2^-24)
 
 // FP64 geometry of one target pixel: source position, intermediate offsets before (U, V) and
 // after (u, v) the inverse SIP. Same arithmetic as the forward FP64 path.
 __device__ __forceinline__ bool fp64_geo(const FwdPlan& P, double X, double Y, double& xs,
                                          double& ys, double& U, double& V, double& u, double& v) {
   if (P.identity) {
-    xs = X;
-    ys = Y;
-    U = u = X - P.crpix_s[0];
-    V = v = Y - P.crpix_s[1];
+    xs = X + P.shift[0];
+    ys = Y + P.shift[1];
+    U = u = X - P.crpix_t[0];
+    V = v = Y - P.crpix_t[1];
     return true;
   }
   double ra, dec;
@@ -113,8 +114,10 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
             const double fx = floor(xs), fy = floor(ys);
             bx = int(fx);
             by = int(fy);
-            xr = float(xs - fx);
-            yr = float(ys - fy);
+            // fractions rounded to FP32 stay below 1, so the taps (and the one-sided slope of
+            // the interpolant) are those of the FP64 floor
+            xr = fminf(float(xs - fx), kBelowOne);
+            yr = fminf(float(ys - fy), kBelowOne);
           }
           U = float(Ud);
           V = float(Vd);

@@ -424,8 +424,8 @@ __device__ __forceinline__ void newton_fp64(const FwdPlan& P, double U, double V
 __device__ __forceinline__ bool source_from_target_fp64(const FwdPlan& P, double X, double Y,
                                                         double& xs, double& ys) {
   if (P.identity) {
-    xs = X;
-    ys = Y;
+    xs = X + P.shift[0];
+    ys = Y + P.shift[1];
     return true;
   }
   double ra, dec, U, V;
@@ -559,13 +559,17 @@ __device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, float X, float 
 // quarter-integers).
 __device__ __forceinline__ void make_anchor(const FwdPlan& P, float X, float Y, Anchor& a) {
   if (P.identity) {
-    a.bx = int32_t(floorf(X));
-    a.by = int32_t(floorf(Y));
-    a.f0x = __fsub_rn(X, floorf(X));
-    a.f0y = __fsub_rn(Y, floorf(Y));
-    // true intermediate offsets of the anchor (used only by the adjoint's chain rule)
-    a.U0 = float(double(X) - P.crpix_s[0]);
-    a.V0 = float(double(Y) - P.crpix_s[1]);
+    // the translation in FP64: exact for the integer and half-integer shifts of dithers
+    const double xs = __dadd_rn(double(X), P.shift[0]), ys = __dadd_rn(double(Y), P.shift[1]);
+    const double fx = floor(xs), fy = floor(ys);
+    a.bx = int32_t(fx);
+    a.by = int32_t(fy);
+    a.f0x = float(__dsub_rn(xs, fx));
+    a.f0y = float(__dsub_rn(ys, fy));
+    // true intermediate offsets of the anchor (the same on both sides; used only by the
+    // adjoint's chain rule)
+    a.U0 = float(double(X) - P.crpix_t[0]);
+    a.V0 = float(double(Y) - P.crpix_t[1]);
     a.a0 = 1.f; a.a1 = 0.f; a.b0 = 0.f; a.b1 = 1.f;
     a.g20 = a.g21 = 0.f;
     a.h2 = 1.f;

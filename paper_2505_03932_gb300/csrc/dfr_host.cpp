@@ -199,9 +199,8 @@ double poly_eval(const double c[10][10], int order, double u, double v) {
   return s;
 }
 
-bool same_linear(const dfr_wcs& a, const dfr_wcs& b) {
-  return std::memcmp(a.crpix, b.crpix, sizeof(a.crpix)) == 0 &&
-         std::memcmp(a.crval, b.crval, sizeof(a.crval)) == 0 &&
+bool same_projection(const dfr_wcs& a, const dfr_wcs& b) {
+  return std::memcmp(a.crval, b.crval, sizeof(a.crval)) == 0 &&
          std::memcmp(a.cd, b.cd, sizeof(a.cd)) == 0;
 }
 
@@ -425,8 +424,12 @@ int build_plan(const dfr_wcs* src, const dfr_wcs* tgt, const float* img, int64_t
   P.flags = int32_t(flags);
   P.order = order;
   const bool tgt_sip = tgt->a_order > 0 || tgt->b_order > 0;
-  P.identity = same_linear(*src, *tgt) &&
+  // the same projection (CRVAL, CD) and no distortion, or the same one inverted exactly: the
+  // intermediate coordinates agree, so the map is the CRPIX translation
+  P.identity = same_projection(*src, *tgt) &&
                ((!tgt_sip && !src_sip && !src_inv) || (exact && same_sip(*src, *tgt)));
+  P.shift[0] = P.identity ? src->crpix[0] - tgt->crpix[0] : 0.0;
+  P.shift[1] = P.identity ? src->crpix[1] - tgt->crpix[1] : 0.0;
 
   // target
   P.crpix_t[0] = tgt->crpix[0] - 1.0;
@@ -1843,24 +1846,37 @@ struct BwdScratch {
   double* partials = nullptr;
   size_t cap = 0;  // doubles
   int sms = 0;
+  // the scratch is reused by the next call: that call's stream waits for `done` first
+  cudaEvent_t done = nullptr;
+  bool used = false;
+  // batched calls: frames fan out over library-owned streams, forked from and joined into the
+  // caller's stream by events
+  static constexpr int kLanes = 4;
+  cudaStream_t lanes[kLanes] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kLanes] = {};
 };
 std::map<int, BwdScratch> g_bwd;
 
+// One adjoint call, prepared on the host: the forward plan for the same source positions and
+// the kernel's extra arguments (grid and partials pointer still to be set). `trivial`: no
+// kernel to run (empty box, or no outputs asked for); grad_params is then zeroed.
+struct BwdCall {
+  FwdPlan P;
+  BwdExtra B;
+  int np = 0;
+  bool trivial = false;
+};
 
-}  // namespace
-}  // namespace dfr
-
-extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
-                                      const float* src_img, int64_t src_pitch,
-                                      const float* grad_out, int64_t go_pitch, int32_t x0,
-                                      int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
-                                      uint32_t flags, float* grad_src, int64_t gs_pitch,
-                                      double* grad_params, void* stream) {
+int prepare_backward(const dfr_wcs* src, const dfr_wcs* tgt, const float* src_img,
+                     int64_t src_pitch, const float* grad_out, int64_t go_pitch, int32_t x0,
+                     int32_t y0, int32_t out_w, int32_t out_h, int32_t order, uint32_t flags,
+                     float* grad_src, int64_t gs_pitch, double* grad_params, BwdCall& C) {
   if (flags & DFR_NAN_MASK)
     return fail(DFR_ERR_INVALID_ARG, "DFR_NAN_MASK is not supported by the adjoint");
   if (order == DFR_BSPLINE3)
     return fail(DFR_ERR_INVALID_ARG, "DFR_BSPLINE3 is not supported by the adjoint");
-  FwdPlan P;
+  FwdPlan& P = C.P;
   // the forward plan (outputs unused) gives the same source positions as dfr_reproject; the
   // split path stages source and gradient boxes by tile, as sized by the plan
   float* dummy = reinterpret_cast<float*>(uintptr_t(16));
@@ -1876,7 +1892,7 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
       return fail(DFR_ERR_INVALID_ARG, "grad_src pitch < NAXIS1");
   }
   P.out = nullptr;
-  BwdExtra B;
+  BwdExtra& B = C.B;
   std::memset(&B, 0, sizeof(B));
   B.grad_src = grad_src;
   B.gs_pitch = gs_pitch;
@@ -1887,11 +1903,11 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
   const bool exact = (flags & DFR_EXACT_INVERSE) && (src->a_order > 0 || src->b_order > 0);
   B.fd = exact ? forward_round_degree(std::max(src->a_order, src->b_order)) : 0;
   // padded layout -> public layout
-  const int np = backward_num_padded(B.fd);
+  C.np = backward_num_padded(B.fd);
   for (int k = 0; k < kMaxParams; ++k) B.pmap[k] = -1;
   for (int k = 0; k < 6; ++k) B.pmap[k] = int16_t(k);
   if (B.fd > 0) {
-    const int nt = (np - 6) / 2;
+    const int nt = (C.np - 6) / 2;
     int t = 0, ia = 6;
     const int ntA = src->a_order > 0 ? (src->a_order + 1) * (src->a_order + 2) / 2 - 1 : 0;
     int ib = 6 + ntA;
@@ -1901,44 +1917,163 @@ extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
         if (n <= src->b_order) B.pmap[6 + nt + t] = int16_t(ib++);
       }
   }
-  if (out_w == 0 || out_h == 0 || (!grad_src && !grad_params)) {
-    if (grad_params) {
-      cudaError_t e = cudaMemsetAsync(grad_params, 0, sizeof(double) * size_t(B.nout),
-                                      static_cast<cudaStream_t>(stream));
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    }
-    return DFR_OK;
+  C.trivial = out_w == 0 || out_h == 0 || (!grad_src && !grad_params);
+  B.box_floats = box_floats(P);
+  return DFR_OK;
+}
+
+// Grid of a prepared call (CTAs resident at once, each striding over its share of the work).
+void backward_grid(BwdCall& C, int sms) {
+  const FwdPlan& P = C.P;
+  BwdExtra& B = C.B;
+  const int smem = backward_smem_bytes(P, B.fd, B.box_floats);
+  if (smem > 0) {
+    // tile-staged kernel: units of kBwdCellsPerCta cells
+    const int units = (P.cells_x * P.cells_y + kBwdCellsPerCta - 1) / kBwdCellsPerCta;
+    const int per_sm = backward_max_blocks_per_sm(P, B.fd, smem);
+    B.grid = std::max(1, std::min(units, sms * per_sm));
+  } else {
+    const int ntiles = P.tiles_x * P.tiles_y;
+    const int per_sm = std::min(4, backward_max_blocks_per_sm(P, B.fd, 0));
+    B.grid = std::max(1, std::min(ntiles, sms * per_sm));
   }
-  std::lock_guard<std::mutex> lock(g_mu);
+}
+
+// The device's scratch, ready for `need` doubles of partial sums, with stream s ordered after
+// the previous call that used it.
+int bwd_scratch(BwdScratch*& out, size_t need, cudaStream_t s) {
   int dev = 0;
   DFR_CUDA(cudaGetDevice(&dev));
   BwdScratch& S = g_bwd[dev];
   if (S.sms == 0) DFR_CUDA(cudaDeviceGetAttribute(&S.sms, cudaDevAttrMultiProcessorCount, dev));
-  B.box_floats = box_floats(P);
-  const int smem = backward_smem_bytes(P, B.fd, B.box_floats);
-  if (smem > 0) {
-    // tile-staged kernel: CTAs resident at once stride over units of kCellsPerCta cells
-    const int units = (P.cells_x * P.cells_y + kBwdCellsPerCta - 1) / kBwdCellsPerCta;
-    const int per_sm = backward_max_blocks_per_sm(P, B.fd, smem);
-    B.grid = std::max(1, std::min(units, S.sms * per_sm));
-  } else {
-    const int ntiles = P.tiles_x * P.tiles_y;
-    const int per_sm = std::min(4, backward_max_blocks_per_sm(P, B.fd, 0));
-    B.grid = std::max(1, std::min(ntiles, S.sms * per_sm));
-  }
-  if (grad_params) {
-    const size_t need = size_t(B.grid) * size_t(np);
-    if (need > S.cap) {
-      if (S.partials) cudaFree(S.partials);
-      S.partials = nullptr;
-      S.cap = 0;
-      DFR_CUDA(cudaMalloc(&S.partials, need * sizeof(double)));
-      S.cap = need;
+  if (!S.done) DFR_CUDA(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+  if (S.used) DFR_CUDA(cudaStreamWaitEvent(s, S.done, 0));
+  if (need > S.cap) {
+    // the previous call's kernels may still read the old buffer: free it after them
+    if (S.partials) {
+      DFR_CUDA(cudaEventSynchronize(S.done));
+      cudaFree(S.partials);
     }
-    B.partials = S.partials;
+    S.partials = nullptr;
+    S.cap = 0;
+    DFR_CUDA(cudaMalloc(&S.partials, need * sizeof(double)));
+    S.cap = need;
   }
-  cudaError_t e = launch_backward(P, B, static_cast<cudaStream_t>(stream));
+  out = &S;
+  return DFR_OK;
+}
+
+int zero_params(const BwdCall& C, cudaStream_t s) {
+  if (!C.B.grad_params) return DFR_OK;
+  cudaError_t e = cudaMemsetAsync(C.B.grad_params, 0, sizeof(double) * size_t(C.B.nout), s);
+  return e == cudaSuccess ? DFR_OK : cuda_fail(e, "cudaMemsetAsync");
+}
+
+}  // namespace
+}  // namespace dfr
+
+extern "C" int dfr_reproject_backward(const dfr_wcs* src, const dfr_wcs* tgt,
+                                      const float* src_img, int64_t src_pitch,
+                                      const float* grad_out, int64_t go_pitch, int32_t x0,
+                                      int32_t y0, int32_t out_w, int32_t out_h, int32_t order,
+                                      uint32_t flags, float* grad_src, int64_t gs_pitch,
+                                      double* grad_params, void* stream) {
+  BwdCall C;
+  int rc = prepare_backward(src, tgt, src_img, src_pitch, grad_out, go_pitch, x0, y0, out_w,
+                            out_h, order, flags, grad_src, gs_pitch, grad_params, C);
+  if (rc != DFR_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (C.trivial) return zero_params(C, s);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  DFR_CUDA(cudaGetDevice(&dev));
+  int sms = g_bwd[dev].sms;
+  if (sms == 0) DFR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  backward_grid(C, sms);
+  BwdScratch* S = nullptr;
+  rc = bwd_scratch(S, grad_params ? size_t(C.B.grid) * size_t(C.np) : 0, s);
+  if (rc != DFR_OK) return rc;
+  if (grad_params) C.B.partials = S->partials;
+  cudaError_t e = launch_backward(C.P, C.B, s);
   if (e != cudaSuccess) return cuda_fail(e, "dfr_reproject_backward launch");
+  DFR_CUDA(cudaEventRecord(S->done, s));
+  S->used = true;
+  return DFR_OK;
+}
+
+extern "C" int dfr_reproject_backward_batch(const dfr_bwd_frame* frames, int32_t n,
+                                            const dfr_wcs* tgt, int32_t order, uint32_t flags,
+                                            void* stream) {
+  if (n < 0) return fail(DFR_ERR_INVALID_ARG, "negative frame count");
+  if (n == 0) return DFR_OK;
+  if (!frames) return fail(DFR_ERR_INVALID_ARG, "NULL frame array");
+  if (n > (1 << 20)) return fail(DFR_ERR_INVALID_ARG, "too many frames");
+  std::vector<BwdCall> calls(static_cast<size_t>(n));
+  for (int f = 0; f < n; ++f) {
+    const dfr_bwd_frame& fr = frames[f];
+    int rc = prepare_backward(&fr.wcs, tgt, fr.img, fr.pitch, fr.grad_out, fr.go_pitch, fr.x0,
+                              fr.y0, fr.w, fr.h, order, flags, fr.grad_src, fr.gs_pitch,
+                              fr.grad_params, calls[size_t(f)]);
+    if (rc != DFR_OK) {
+      g_err = "frame " + std::to_string(f) + ": " + g_err;
+      return rc;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  DFR_CUDA(cudaGetDevice(&dev));
+  int sms = g_bwd[dev].sms;
+  if (sms == 0) DFR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // every frame that writes parameter gradients gets its own slice of the partial sums
+  std::vector<size_t> off(static_cast<size_t>(n), 0);
+  size_t need = 0;
+  for (int f = 0; f < n; ++f) {
+    BwdCall& C = calls[size_t(f)];
+    if (C.trivial) continue;
+    backward_grid(C, sms);
+    off[size_t(f)] = need;
+    if (C.B.grad_params) need += size_t(C.B.grid) * size_t(C.np);
+  }
+  BwdScratch* S = nullptr;
+  int rc = bwd_scratch(S, need, s);
+  if (rc != DFR_OK) return rc;
+  if (!S->fork) {
+    DFR_CUDA(cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
+    for (int l = 0; l < BwdScratch::kLanes; ++l) {
+      DFR_CUDA(cudaStreamCreateWithFlags(&S->lanes[l], cudaStreamNonBlocking));
+      DFR_CUDA(cudaEventCreateWithFlags(&S->join[l], cudaEventDisableTiming));
+    }
+  }
+  for (int f = 0; f < n; ++f)
+    if (calls[size_t(f)].trivial) {
+      rc = zero_params(calls[size_t(f)], s);
+      if (rc != DFR_OK) return rc;
+    }
+  // frames in kLanes chains side by side (frame f on lane f mod kLanes), after the caller's
+  // earlier work and before its later work
+  DFR_CUDA(cudaEventRecord(S->fork, s));
+  const int lanes = std::min(n, BwdScratch::kLanes);
+  for (int l = 0; l < lanes; ++l) DFR_CUDA(cudaStreamWaitEvent(S->lanes[l], S->fork, 0));
+  cudaError_t err = cudaSuccess;
+  int bad = -1;
+  for (int f = 0; f < n && err == cudaSuccess; ++f) {
+    BwdCall& C = calls[size_t(f)];
+    if (C.trivial) continue;
+    if (C.B.grad_params) C.B.partials = S->partials + off[size_t(f)];
+    err = launch_backward(C.P, C.B, S->lanes[f % lanes]);
+    if (err != cudaSuccess) bad = f;
+  }
+  // join every lane back, also after a failed launch (the caller's stream stays ordered)
+  for (int l = 0; l < lanes; ++l) {
+    DFR_CUDA(cudaEventRecord(S->join[l], S->lanes[l]));
+    DFR_CUDA(cudaStreamWaitEvent(s, S->join[l], 0));
+  }
+  DFR_CUDA(cudaEventRecord(S->done, s));
+  S->used = true;
+  if (err != cudaSuccess)
+    return fail(DFR_ERR_CUDA, "frame %d: dfr_reproject_backward_batch launch: %s", bad,
+                cudaGetErrorString(err));
   return DFR_OK;
 }
 

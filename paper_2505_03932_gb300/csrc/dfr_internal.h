@@ -69,7 +69,9 @@ struct FwdPlan {  // aligned (128 B) through its CUtensorMap member, as TMA requ
   int32_t tma_ok;            // box staging the source allows: 1 TMA, 2 asynchronous copies, 0 none
   float jac[4];              // host bounds of |dx/dX|, |dx/dY|, |dy/dX|, |dy/dY| (box sizing)
   float curv[3];             // host bounds of the map's second derivatives (xx, xy, yy)
-  int32_t identity;          // source and target WCS are bitwise equal
+  int32_t identity;          // the map is a translation: source and target WCS differ at
+                             // most in CRPIX (same CRVAL, CD and distortion)
+  double shift[2];           // then x_s = x_t + shift (source minus target CRPIX)
   // target WCS
   double crpix_t[2];         // CRPIX - 1 (0-based reference pixel)
   int32_t tsip_deg;          // 0 = no target SIP; else packed degree of A, B

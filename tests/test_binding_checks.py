@@ -45,3 +45,11 @@ def test_footprint_must_match_value_plane():
 def test_noalloc_bspline_needs_prefiltered_coefficients():
     with pytest.raises(ValueError, match="prefiltered"):
         dfr.reproject_batch_noalloc([], [], _wcs(8, 8), [], [], order="bspline3")
+
+
+def test_backward_batch_lists_must_agree():
+    w = _wcs(8, 8)
+    with pytest.raises(ValueError, match="same length"):
+        dfr.reproject_backward_batch([None, None], [w], w, [None, None], [(0, 0, 8, 8)] * 2)
+    with pytest.raises(ValueError, match="one entry per frame"):
+        dfr.reproject_backward_batch([None], [w], w, [None], [(0, 0, 8, 8)], grad_srcs=[])

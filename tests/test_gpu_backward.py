@@ -142,6 +142,98 @@ def test_config3_window_gradients():
         _group_check(gp.cpu().numpy(), g_ref, names)
 
 
+@pytest.mark.parametrize("order,precision,exact", [("bilinear", "split", False),
+                                                   ("bicubic", "split", True),
+                                                   ("bicubic", "fp64", False),
+                                                   ("lanczos3", "split", False)])
+def test_backward_batch_equals_single_calls(order, precision, exact):
+    """dfr_reproject_backward_batch over frames of uneven sizes, rotations and boxes (one of them
+    empty, one sharing another's grad_src) against one dfr_reproject_backward call per frame:
+    grad_params bit for bit, grad_src to float-atomic ordering (1e-6 of its scale)."""
+    rng = synth.rng_for(31)
+    tgt = synth.tan_wcs(600, 520, rho_deg=1.5, crpix=(300.5, 260.5))
+    specs = [(300, 220, 0.0, (7, 3, 291, 237)), (420, 380, 2.0, None), (128, 96, -1.0, None),
+             (256, 256, 0.5, (0, 0, 0, 0)), (300, 220, 0.0, (40, 60, 200, 180))]
+    srcs, imgs, boxes, gos = [], [], [], []
+    for k, (w, h, rho, bb) in enumerate(specs):
+        s = synth.add_sip(synth.tan_wcs(w, h, rho_deg=rho), 3, 1e-6, rng)
+        s["a"] *= 50.0
+        s["b"] *= 50.0
+        s, _ = OW.with_inverse_sip(s, 4)
+        if k == 4:  # frame 4 reprojects frame 0's image with frame 0's WCS over another box
+            s = srcs[0]
+        srcs.append(s)
+        imgs.append(imgs[0] if k == 4 else to_dev(synth.sky_image(w, h, 20, rng)))
+        box = bb if bb is not None else dfr().target_bbox(s, tgt)
+        boxes.append(box)
+        gos.append(to_dev(synth.rng_for(40 + k).standard_normal((max(box[3], 1),
+                                                                   max(box[2], 1)))
+                          .astype(np.float32)))
+    T = torch()
+    gs_b = [T.zeros_like(i) for i in imgs]
+    gs_b[4] = gs_b[0]  # shared: frames 0 and 4 add into one buffer
+    gs_b, gp_b = dfr().reproject_backward_batch(imgs, srcs, tgt, gos, boxes, order, precision,
+                                                exact_inverse=exact, grad_srcs=gs_b)
+    T.cuda.synchronize()
+    dfr().device_status()
+    gs_s = [T.zeros_like(i) for i in imgs]
+    gs_s[4] = gs_s[0]
+    gp_s = []
+    for k in range(len(imgs)):
+        _, gp = dfr().reproject_backward(imgs[k], srcs[k], tgt, gos[k], boxes[k], order,
+                                         precision, exact_inverse=exact, grad_src=gs_s[k])
+        gp_s.append(gp)
+    T.cuda.synchronize()
+    for k in range(len(imgs)):
+        assert T.equal(gp_b[k], gp_s[k]), k
+        a, b = gs_b[k].cpu().numpy(), gs_s[k].cpu().numpy()
+        scale = np.abs(b).max()
+        if k == 3:  # the empty box: nothing scattered, parameters zero
+            assert scale == 0.0 and float(gp_b[k].abs().sum()) == 0.0
+            continue
+        assert scale > 0
+        assert np.abs(a - b).max() <= 1e-6 * scale, k
+
+
+def test_config3_whole_frame_sampled_gradients():
+    """The 2048^2 differentiation case over the whole frame: the loss gradient of a seeded 1 %
+    sample of the target pixels (grad_out = 2 (O - ref) there, zero elsewhere, so the launch
+    covers every cell of the frame), against the oracle's dual numbers summed over the same
+    pixels (CRVAL, CD and the 18 SIP terms, Newton inverse)."""
+    c = synth.config3()
+    src = c["src"][0]
+    src, _ = OW.with_inverse_sip(src, 4)
+    pert = synth.copy_wcs(c["perturbed"])
+    pert["ap"], pert["bp"], pert["ap_order"], pert["bp_order"] = src["ap"], src["bp"], 4, 4
+    tgt, img = c["tgt"], c["images"][0]
+    n = 2048
+    rng = synth.rng_for(303)
+    idx = rng.choice(n * n, n * n // 100, replace=False)
+    X = (idx % n).astype(np.float64)
+    Y = (idx // n).astype(np.float64)
+    # Bilinear interpolation has kinks on the integer lines of the source grid, where its
+    # derivative jumps: a pixel whose position lies within the split path's position error of
+    # such a line may take the slope of the other side (both are derivatives of the same
+    # continuous output). Such pixels (1e-4 px margin, about 4e-4 of the sample) are left out.
+    sx, sy, _ = OR.coords(src, tgt, X, Y, inverse="newton")
+    far = (np.abs(sx - np.rint(sx)) > 1e-4) & (np.abs(sy - np.rint(sy)) > 1e-4)
+    idx, X, Y = idx[far], X[far], Y[far]
+    ref, _, _, _ = OR.reproject_pixels(pert, tgt, img, X, Y, "bilinear", inverse="newton")
+    o, names = OD.reproject_dual(src, tgt, img, X, Y, "bilinear")
+    r = o.v - ref
+    g_ref = (2.0 * r * o.d).sum(axis=1)
+    go = np.zeros(n * n, np.float32)
+    go[idx] = (2.0 * r).astype(np.float32)
+    go = go.reshape(n, n)
+    for precision in ("fp64", "split"):
+        _, gp = dfr().reproject_backward(to_dev(img), src, tgt, to_dev(go), (0, 0, n, n),
+                                         "bilinear", precision, exact_inverse=True,
+                                         want_src=False)
+        torch().cuda.synchronize()
+        dfr().device_status()
+        _group_check(gp.cpu().numpy(), g_ref, names)
+
+
 def test_autograd_alignment_descent():
     """torch.autograd through dfr: fitting CRVAL by gradient descent recovers a 0.3 arcsec
     offset of the reference image."""

@@ -103,6 +103,25 @@ def test_integer_shift_nearest_bit_exact(precision):
     assert set(np.unique(fp)) <= {0.0, 1.0}
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_half_pixel_shift_nearest_ties_round_up(precision):
+    """A CRPIX shift of (-0.5, +1.5) px with the same sky projection: every source position is
+    exactly halfway between two pixel centres, and nearest takes the upper one (floor(x + 0.5)),
+    as the oracle does on the same positions."""
+    c = synth.config0()
+    src, img = c["src"][0], c["images"][0]
+    tgt = synth.copy_wcs(src)
+    tgt["crpix"] = (src["crpix"][0] - 0.5, src["crpix"][1] + 1.5)
+    val, fp, cr = gpu(src, tgt, to_dev(img), "nearest", precision, (0, 0, 512, 512))
+    Y, X = np.mgrid[0:512, 0:512].astype(np.float64)
+    assert np.array_equal(cr[..., 0], X + 0.5) and np.array_equal(cr[..., 1], Y - 1.5)
+    exp = np.zeros_like(img)
+    exp[1:, :511] = img[:511, 1:]
+    assert np.array_equal(val, exp)
+    ov, ofp = OI.interpolate(img, X + 0.5, Y - 1.5, OI.NEAREST)
+    assert np.array_equal(val, ov.astype(np.float32)) and np.array_equal(fp, ofp.astype(np.float32))
+
+
 def test_linear_ramp_bilinear_and_quadratic_bicubic():
     c = synth.config0()
     src, tgt = c["src"][0], c["tgt"]

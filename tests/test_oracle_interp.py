@@ -46,6 +46,28 @@ def test_nearest_integer_shift_bit_exact():
     assert np.array_equal(fp != 0, exp != 0)
 
 
+def test_nearest_half_pixel_ties_round_up():
+    """Positions exactly halfway between pixel centres go to the upper pixel (index
+    floor(x + 0.5)); round-half-even or round-half-down would pick the lower one at every other
+    (or every) column. At x = W - 0.5 the position is covered but its pixel lies outside the
+    image: value and footprint 0."""
+    rng = synth.rng_for(31)
+    img = rng.standard_normal((40, 50)).astype(np.float32)
+    Y, X = np.mgrid[0:40, 0:50].astype(np.float64)
+    val, fp = I.interpolate(img, X + 0.5, Y - 1.5, I.NEAREST)
+    exp = np.zeros((40, 50))
+    exp[1:, :49] = img[:39, 1:]
+    assert np.array_equal(val, exp)
+    efp = np.zeros((40, 50))
+    efp[1:, :49] = 1.0
+    assert np.array_equal(fp, efp)
+    # negative half: -0.5 is covered and rounds up to pixel 0
+    v, f = I.interpolate(img, np.array([-0.5, 0.5, 1.5, 2.5]), np.array([0.0, 0.0, 0.0, 0.0]),
+                         I.NEAREST)
+    assert np.array_equal(v, img[0, [0, 1, 2, 3]].astype(np.float64))
+    assert np.array_equal(f, np.ones(4))
+
+
 @pytest.mark.parametrize("order", [I.NEAREST, I.BILINEAR, I.BICUBIC])
 def test_identity_bit_exact(order):
     rng = synth.rng_for(31)
