@@ -321,17 +321,19 @@ __device__ __forceinline__ uint32_t box_token() {
 // fractions, weights, and the tap sums, each half the exact operation sequence of the
 // per-pixel path (interp_pixel), so both give the same bits. The box pitch is the
 // compile-time kBoxW: a pixel's taps are immediate offsets from one shared address.
-// EDGE: the tile's taps may leave the image (the box holds zeros there, the TMA fill): per pixel
+// edge: the tile's taps may leave the image (the box holds zeros there, the TMA fill): per pixel
 // also the coverage test and, unless all its taps are inside, the in-image weight sums as
 // footprint and value = sum / footprint, as interp_pixel does (the zero taps add nothing to
-// the sum, exactly like the zeroed weights there).
-template <int ORDER, bool ACC, int TH, bool FP, bool EDGE>
+// the sum, exactly like the zeroed weights there). fp: the footprint plane is written. Both are
+// uniform runtime branches (one copy of the loop: a smaller kernel, at the same speed).
+template <int ORDER, bool ACC, int TH>
 __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a,
                                                     const ColCubic& cc, int gx, int oy, int r0,
-                                                    uint32_t sbox, const TileBox& tb) {
+                                                    uint32_t sbox, const TileBox& tb,
+                                                    const bool fp, const bool edge) {
   using T = Taps<ORDER>;
   constexpr int n = T::n;
-  // EDGE: absolute first-tap column/row = floor bits + (bx + lo - magic bits); coverage bounds
+  // edge: absolute first-tap column/row = floor bits + (bx + lo - magic bits); coverage bounds
   const int kxa = a.bx + T::lo - int(kFloorMagicBits), kya = a.by + T::lo - int(kFloorMagicBits);
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
@@ -347,7 +349,7 @@ __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a
   const float2 magic = v_c<float2>(kFloorMagic);
   const int64_t pitch = Q.out_pitch;
   float* po = Q.out + int64_t(oy) * pitch + gx;
-  float* pf = FP ? Q.fp + int64_t(oy) * pitch + gx : nullptr;
+  float* pf = fp ? Q.fp + int64_t(oy) * pitch + gx : nullptr;
   float2 s = make_float2(float(r0) - kCellMid, float(r0 + 1) - kCellMid);
 #pragma unroll 2
   for (int i = 0; i < TH / 2; ++i) {
@@ -394,7 +396,7 @@ __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a
       }
     }
     float2 fpv = make_float2(1.f, 1.f);
-    if (EDGE) {
+    if (edge) {
       // per pixel (half h = A, B): coverage, interior taps, else in-image weight sums
       float v2[2] = {num.x, num.y}, f2[2] = {1.f, 1.f};
 #pragma unroll
@@ -436,13 +438,13 @@ __device__ __forceinline__ void tile_rows_fast_impl(const HP& Q, const Anchor& a
     } else {
       __stcs(po, num.x);
       __stcs(po + pitch, num.y);
-      if (FP) {
+      if (fp) {
         __stcs(pf, fpv.x);
         __stcs(pf + pitch, fpv.y);
       }
     }
     po += 2 * pitch;
-    if (FP) pf += 2 * pitch;
+    if (fp) pf += 2 * pitch;
     s = v_add(s, make_float2(2.f, 2.f));
   }
 }
@@ -451,17 +453,8 @@ template <int ORDER, bool ACC, int TH>
 __device__ __forceinline__ void tile_rows_fast(const HP& Q, const Anchor& a, const ColCubic& cc,
                                                int gx, int oy, int r0, uint32_t sbox,
                                                const TileBox& tb) {
-  if (tb.interior) {
-    if (ACC || Q.fp)
-      tile_rows_fast_impl<ORDER, ACC, TH, true, false>(Q, a, cc, gx, oy, r0, sbox, tb);
-    else
-      tile_rows_fast_impl<ORDER, ACC, TH, false, false>(Q, a, cc, gx, oy, r0, sbox, tb);
-  } else {
-    if (ACC || Q.fp)
-      tile_rows_fast_impl<ORDER, ACC, TH, true, true>(Q, a, cc, gx, oy, r0, sbox, tb);
-    else
-      tile_rows_fast_impl<ORDER, ACC, TH, false, true>(Q, a, cc, gx, oy, r0, sbox, tb);
-  }
+  tile_rows_fast_impl<ORDER, ACC, TH>(Q, a, cc, gx, oy, r0, sbox, tb, ACC || Q.fp != nullptr,
+                                      !tb.interior);
 }
 
 // General rows of a tile (per pixel): position (column cubic or exact), coverage, then the
