@@ -83,4 +83,23 @@ __device__ __forceinline__ void chain_terms(const FwdPlan& P, const ChainConst& 
   c[5] = -ny * V;
 }
 
+// The same chain rule with M given (its entries m00, m01, m10, m11): the CRVAL and CD terms
+// from dL/d(source position) through M, CD^-1 and the TAN projection.
+__device__ __forceinline__ void chain_terms_m(const ChainConst& K, float gxs, float gys, float U,
+                                              float V, float m00, float m01, float m10,
+                                              float m11, float& lu, float& lv, float c[6]) {
+  lu = fmaf(gxs, m00, gys * m10);
+  lv = fmaf(gxs, m01, gys * m11);
+  const float nx = fmaf(K.ci00, lu, K.ci10 * lv);
+  const float ny = fmaf(K.ci01, lu, K.ci11 * lv);
+  const float xi = fmaf(K.cd00, U, K.cd01 * V) / kR0f;
+  const float eta = fmaf(K.cd10, U, K.cd11 * V) / kR0f;
+  c[0] = nx * fmaf(-K.cd0, fmaf(xi, xi, 1.f), K.sd0 * eta) + ny * (-xi * fmaf(K.cd0, eta, K.sd0));
+  c[1] = nx * (-xi * eta) + ny * (-fmaf(eta, eta, 1.f));
+  c[2] = -nx * U;
+  c[3] = -nx * V;
+  c[4] = -ny * U;
+  c[5] = -ny * V;
+}
+
 }  // namespace dfr

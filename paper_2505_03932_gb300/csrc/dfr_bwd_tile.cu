@@ -2,7 +2,8 @@
 //
 // Work decomposition: kBwdCellsPerCta 32x64 cells per CTA, one per warp, each cell as 8 tiles
 // of 32x8 (lane = column); source positions from the same cell fits as the forward kernels
-// (bit for bit). Per tile the source box is
+// (bit for bit). The chain rule's inverse-SIP Jacobian comes from per-cell cubics as well
+// (fit_jacobian), for the polynomial and the Newton inverse. Per tile the source box is
 // staged by TMA into the warp's shared buffer (the taps are read from it) and a second buffer
 // of the same shape collects the tile's dL/dS contributions with shared-memory atomics; the
 // buffer is then added to grad_src with one global atomic per non-zero element (instead of one
@@ -17,12 +18,108 @@
 
 namespace dfr {
 
+// Source intermediate offsets (U, V) of target offset (dx, dy) from the anchor: the part of
+// split_coords_core before the inverse SIP, with the same operations (so the same bits as its
+// geo[0], geo[1] added to the anchor's (U0, V0)).
+__device__ __forceinline__ void split_uv(const FwdPlan& P, const HP& Q, const Anchor& a, float dx,
+                                         float dy, float& U, float& V) {
+  if (Q.identity) {
+    U = a.U0 + dx;
+    V = a.V0 + dy;
+    return;
+  }
+  float dp = dx, dq = dy;
+  if (Q.tsip) {
+    float fa, fb;
+    tsip_pair(P, __fadd_rn(a.tu, dx), __fadd_rn(a.tv, dy), fa, fb);
+    dp = __fadd_rn(dx, __fsub_rn(fa, a.tA));
+    dq = __fadd_rn(dy, __fsub_rn(fb, a.tB));
+  }
+  const float nu = fmaf(a.a0, dp, __fmul_rn(a.a1, dq));
+  const float nv = fmaf(a.b0, dp, __fmul_rn(a.b1, dq));
+  const float den = fmaf(a.g20, dp, fmaf(a.g21, dq, a.h2));
+  const float rcp = __fdividef(1.f, den);
+  U = a.U0 + __fmul_rn(nu, rcp);
+  V = a.V0 + __fmul_rn(nv, rcp);
+}
+
+// The inverse-SIP Jacobian M = d(u, v)/d(U, V) over a cell, as the positions are: sampled at
+// the 4x4 Lobatto nodes (lane i + 4 j), interpolated across the columns by the Lagrange
+// weights and fitted by a cubic in s per column. Polynomial inverse (FD = 0): M = I +
+// d(AP, BP)/d(U, V), a polynomial of one degree less than AP/BP in (U, V); Newton inverse: M =
+// (I + d(A, B)/d(u, v))^-1 at the node's exact solution (u, v). Either is a smooth function of
+// the pixel, which the cubics reproduce to FP32 rounding for polynomials up to degree 4 and
+// closely beyond; the per-pixel chain rule then evaluates two cubics instead of polynomial
+// gradients (and, with the Newton inverse, instead of the Newton solve).
+struct JacCubic {
+  float2 r0[4], r1[4];  // (m00, m01) and (m10, m11) coefficients in s
+};
+
+template <int IDEG, int FD>
+__device__ __forceinline__ JacCubic fit_jacobian(const FwdPlan& P, const HP& Q, const Anchor& a,
+                                                 int lane) {
+  const unsigned full = 0xffffffffu;
+  float m00 = 1.f, m01 = 0.f, m10 = 0.f, m11 = 1.f;
+  if (lane < 16) {
+    const float2 p = cell_sample(lane);
+    float A, Au, Av, Bq, Bu, Bv;
+    if (FD == 0) {
+      float U, V;
+      split_uv(P, Q, a, p.x - 0.5f, p.y, U, V);
+      poly_grad<IDEG, float>(P.isip_f[0], P.isip_deg, U, V, A, Au, Av);
+      poly_grad<IDEG, float>(P.isip_f[1], P.isip_deg, U, V, Bq, Bu, Bv);
+      m00 = 1.f + Au;
+      m01 = Av;
+      m10 = Bu;
+      m11 = 1.f + Bv;
+    } else {
+      float xe, ye, geo[4];
+      split_coords_core<IDEG, false, FD>(P, nullptr, Q.identity, Q.tsip, Q.newton, a,
+                                         p.x - 0.5f, p.y, xe, ye, geo);
+      const float u = a.U0 + geo[2], v = a.V0 + geo[3];
+      poly_grad<FD, float>(P.fsip_f[0], P.fsip_deg, u, v, A, Au, Av);
+      poly_grad<FD, float>(P.fsip_f[1], P.fsip_deg, u, v, Bq, Bu, Bv);
+      const float j00 = 1.f + Au, j01 = Av, j10 = Bu, j11 = 1.f + Bv;
+      const float inv = __fdividef(1.f, fmaf(j00, j11, -j01 * j10));
+      m00 = j11 * inv;
+      m01 = -j01 * inv;
+      m10 = -j10 * inv;
+      m11 = j00 * inv;
+    }
+  }
+  float L[4];
+  lagrange_x(float(lane) - 15.5f, L);
+  float2 g0[4], g1[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int src = i + 4 * j;
+      const float2 f0 = make_float2(__shfl_sync(full, m00, src), __shfl_sync(full, m01, src));
+      const float2 f1 = make_float2(__shfl_sync(full, m10, src), __shfl_sync(full, m11, src));
+      const float2 Li = make_float2(L[i], L[i]);
+      g0[j] = i == 0 ? v_mul(Li, f0) : v_fma(Li, f0, g0[j]);
+      g1[j] = i == 0 ? v_mul(Li, f1) : v_fma(Li, f1, g1[j]);
+    }
+  }
+  JacCubic J;
+  fit_s(g0, J.r0);
+  fit_s(g1, J.r1);
+  return J;
+}
+
+__device__ __forceinline__ float2 jac_row(const float2 c[4], float s) {
+  const float2 ss = make_float2(s, s);
+  return v_fma(v_fma(v_fma(c[3], ss, c[2]), ss, c[1]), ss, c[0]);
+}
+
 template <int ORDER, int IDEG, int FD>
 __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, const BwdExtra& B,
                                               const ChainConst& K, const Anchor& a,
                                               const ColCubic& cc, int ox, int oy, int r0,
                                               int lane, const float* box, float* gbox,
-                                              const TileBox& tb, bool want_params, float* acc) {
+                                              const TileBox& tb, bool want_params, float* acc,
+                                              const JacCubic& J) {
   using T = Taps<ORDER>;
   constexpr int NTERM = nterms(FD);
   const int gx = ox + lane;
@@ -30,18 +127,18 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, con
   const float xlo = -0.5f - float(a.bx), xhi = float(Q.W) - 0.5f - float(a.bx);
   const float ylo = -0.5f - float(a.by), yhi = float(Q.H) - 0.5f - float(a.by);
   const float dx0 = float(lane - kAnchorCol);
+  // the anchor base in source intermediate offsets (for u, v of the Newton inverse's terms)
+  const float ub = float(double(a.bx) - P.crpix_s[0]), vb = float(double(a.by) - P.crpix_s[1]);
   const int bw = Q.box_w, bh = Q.box_h;
   const int nrows = min(kTileH, Q.h - oy);
 #pragma unroll 1
   for (int r = 0; r < nrows; ++r) {
-    float x, y, geo[4];
+    float x, y;
+    float U = 0.f, V = 0.f;
     const bool ok = pixel_coords(P, Q, a, cc, lane, r0 + r, x, y);
-    if (want_params) {
-      // the chain rule's intermediate offsets, from the exact per-pixel evaluation
-      float xe, ye;
-      split_coords_core<IDEG, false, FD>(P, nullptr, Q.identity, Q.tsip, Q.newton, a, dx0,
-                                         float(r0 + r) - kCellMid, xe, ye, geo);
-    }
+    // the chain rule's intermediate offsets (U, V) from the local homography; M from the cell's
+    // Jacobian cubics
+    if (want_params) split_uv(P, Q, a, dx0, float(r0 + r) - kCellMid, U, V);
     const bool cov = !tb.empty && ok && x >= xlo && x <= xhi && y >= ylo && y <= yhi;
     float gxs = 0.f, gys = 0.f;
     if (cov) {
@@ -157,10 +254,15 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, con
       }
     }
     if (!want_params || !cov) continue;
-    const float U = a.U0 + geo[0], V = a.V0 + geo[1];
-    const float u = a.U0 + geo[2], v = a.V0 + geo[3];
     float lu, lv, c[6];
-    chain_terms<IDEG, FD>(P, K, cov, Q.newton, gxs, gys, U, V, u, v, lu, lv, c);
+    const float sr = float(r0 + r) - kCellMid;
+    const bool jac = FD > 0 || IDEG != 0;
+    const float2 mr0 = jac ? jac_row(J.r0, sr) : make_float2(1.f, 0.f);
+    const float2 mr1 = jac ? jac_row(J.r1, sr) : make_float2(0.f, 1.f);
+    chain_terms_m(K, gxs, gys, U, V, mr0.x, mr0.y, mr1.x, mr1.y, lu, lv, c);
+    // Newton inverse: the SIP coefficient terms at the pixel's intermediate offsets after the
+    // inverse, u = x_s - CRPIX1 (the position the cell cubic gives), likewise v
+    const float u = ub + x, v = vb + y;
 #pragma unroll
     for (int q = 0; q < 6; ++q) acc[q] += c[q];
     if (FD > 0) {
@@ -236,6 +338,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __gr
       Anchor a;
       const ColCubic cc = cell_fit<false, true>(P, Q, cox, coy, lane, a);
       Q.use_tma = P.use_tma != 0 && !P.stage_sw && !dead;
+      JacCubic J;
+      if ((FD > 0 || IDEG != 0) && want_params) J = fit_jacobian<IDEG, FD>(P, Q, a, lane);
       float acc[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[q] = 0.f;
@@ -258,7 +362,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __gr
           }
         }
         bwd_tile_rows<ORDER, IDEG, FD>(P, Q, B, K, a, cc, cox, oy, k * kTileH, lane, box, gbox,
-                                       tb, want_params, acc);
+                                       tb, want_params, acc, J);
         if (tb.use_box && B.grad_src) {
           __syncwarp();
           flush_gbox(Q, B, tb, gbox, lane);
