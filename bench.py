@@ -469,23 +469,26 @@ def run_gpu(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ other configurations
 def _events_time(fn, k, flush=None):
-    """Median device time (ms, CUDA events around the call) and median host time of the call
-    itself (ms, until it returns)."""
+    """Median device time (ms, CUDA events around each call) and median host time of the call
+    itself (ms, until it returns). The k calls are enqueued back to back (each after the L2
+    flush when one is given), so the host prepares a call while the device runs the previous
+    work: the events time the device work, not the host's preparation of it."""
     import torch
-    ts, hs = [], []
+    evs, hs = [], []
+    torch.cuda.synchronize()
     for _ in range(k):
         if flush is not None:
             flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         a.record()
         t0 = time.perf_counter()
         fn()
         hs.append((time.perf_counter() - t0) * 1e3)
         b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ts = [a.elapsed_time(b) for a, b in evs]
     return float(np.median(ts)), float(np.median(hs))
 
 
@@ -616,6 +619,81 @@ def measure_stack32(dfr, torch, flush, steps):
             "adjoint_bytes_per_pixel": 12}
 
 
+def measure_configs(dfr, torch, flush, steps):
+    """Every workload configuration, split precision and all-FP64, forward with value and
+    footprint: 512^2 TAN bilinear (0), the 4096^2 bench frame (1), the 64-frame batch (2), the
+    2048^2 differentiation frame with the Newton inverse (3) and the 32-frame stack (4). Batches
+    go through dfr_reproject_batch (launch form tuned on the first call of each precision).
+    Per configuration and path: ms, output Mpix/s and the HBM fraction at the algorithmic bytes
+    (source read once + 8 B per output pixel). One dict per configuration."""
+    peak = _peaks()[0]
+    rows = []
+
+    def entry(name, npx, src_bytes, t_split, t_fp64, extra=None):
+        algo = src_bytes + 8 * npx
+        d = {"workload": name, "output_mpix": npx / 1e6}
+        for k, t in (("split", t_split), ("fp64", t_fp64)):
+            d[k] = {"ms": t, "mpix_s": npx / t / 1e3,
+                    "frac_hbm": algo / (t * 1e-3) / 1e9 / peak}
+        d["split_speedup"] = t_fp64 / t_split
+        d.update(extra or {})
+        rows.append(d)
+
+    def single(src, tgt, img, order, exact, bbox, fp64_steps):
+        src = dfr.to_c(src)
+        tgt = dfr.to_c(tgt)
+        img_d = torch.from_numpy(img).cuda()
+        w, h = bbox[2], bbox[3]
+        o = torch.empty((h, w), device="cuda")
+        f = torch.empty_like(o)
+        ts = {}
+        for prec, k in (("split", steps), ("fp64", fp64_steps)):
+            fn = lambda: dfr.reproject(img_d, src, tgt, bbox=bbox, order=order, precision=prec,
+                                       exact_inverse=exact, out=o, fp_out=f)
+            fn()
+            ts[prec] = _events_time(fn, k, flush)[0]
+        return w * h, img.nbytes, ts["split"], ts["fp64"]
+
+    def batch(cfg, ideg, fp64_steps):
+        tgt = dfr.to_c(cfg["tgt"])
+        srcs = [dfr.to_c(dfr.fit_inverse_sip(sw, ideg)[0]) for sw in cfg["src"]]
+        imgs = [torch.from_numpy(i).cuda() for i in cfg["images"]]
+        bbs = [dfr.target_bbox(sw, tgt) for sw in srcs]
+        outs = [torch.empty((b[3], b[2]), device="cuda") for b in bbs]
+        fps = [torch.empty_like(o) for o in outs]
+        ts, tuned = {}, {}
+        for prec, k in (("split", steps), ("fp64", fp64_steps)):
+            fn = lambda: dfr.reproject_batch(imgs, srcs, tgt, bbs, order=cfg["order"],
+                                             precision=prec, outs=outs, fps=fps)
+            fn()
+            torch.cuda.synchronize()
+            tuned[prec] = dfr.last_launch_config()["batch"]
+            ts[prec] = _events_time(fn, k, flush)[0]
+        npx = sum(b[2] * b[3] for b in bbs)
+        return npx, sum(i.numel() * 4 for i in imgs), ts["split"], ts["fp64"], tuned
+
+    c = synth.config0()
+    entry("config 0: 512^2 TAN, bilinear", *single(c["src"][0], c["tgt"], c["images"][0],
+                                                   "bilinear", False, (0, 0, 512, 512), steps))
+    c = synth.config1()
+    src = dfr.fit_inverse_sip(c["src"][0], 4)[0]
+    entry("config 1: 4096^2 TAN-SIP3, bicubic", *single(src, c["tgt"], c["images"][0], "bicubic",
+                                                        False, (0, 0, 4096, 4096), 3))
+    c = synth.config3()
+    src = dfr.fit_inverse_sip(c["src"][0], 4)[0]
+    entry("config 3: 2048^2 TAN-SIP3, bilinear, Newton inverse",
+          *single(src, c["tgt"], c["images"][0], "bilinear", True, (0, 0, 2048, 2048), 3))
+    del c
+    npx, sb, t1, t2, tuned = batch(synth.config2(), 4, 2)
+    entry("config 2: 64 frames (2048-6144 px, SIP3) -> 8192^2, bilinear", npx, sb, t1, t2,
+          {"tuned": tuned})
+    npx, sb, t1, t2, tuned = batch(synth.config4(), 6, 2)
+    entry("config 4: 32 x 6000x4000 SIP5 -> 12000x8000, bicubic", npx, sb, t1, t2,
+          {"tuned": tuned})
+    dfr.device_status()
+    return rows
+
+
 def run_oracle(args):
     """The FP64 CPU oracle, as it stands, in one process on each configuration (no GPU):
     whole frames for the 512^2 and 2048^2 cases, 1M random pixels of the 4096^2 frame, and a
@@ -726,6 +804,8 @@ def run_extra(args):
                     "forward_mpix_s": 4.194304 / t_f * 1e3, "adjoint_mpix_s": 4.194304 / t_b * 1e3})
     if args.workload in ("stack32", "all"):
         out.append(measure_stack32(dfr, torch, flush, max(3, args.steps // 2)))
+    if args.workload in ("configs", "all"):
+        out.extend(measure_configs(dfr, torch, flush, max(3, min(args.steps, 10))))
     if args.workload in ("adjoint6000", "all"):
         # one 6000x4000 SIP5 exposure of the stack configuration: forward, adjoint with the
         # polynomial inverse (CRVAL and CD gradients), adjoint with the Newton inverse (A/B too)
@@ -846,6 +926,7 @@ def main():
                     help="leave out the batch and adjoint keys of the bench line")
     ap.add_argument("--workload", default="sip3_4096",
                     choices=["sip3_4096", "batch64", "grad2048", "stack32", "adjoint6000", "coadd32",
+                             "configs",
                              "tsip4096", "lanczos4096", "bspline4096", "all", "oracle"],
                     help="sip3_4096: the bench line; the others print secondary measurements "
                          "(oracle: the CPU oracle on every configuration, no GPU)")
