@@ -494,8 +494,9 @@ def _events_time(fn, k, flush=None):
 
 def measure_batch64(dfr, torch, flush, steps):
     """The batch configuration: 64 exposures (long side 2048-6144 px, SIP3) onto one 8192^2
-    target, bilinear, split precision, value and footprint; dfr_reproject_batch (one CUDA-graph
-    or persistent launch, tuned on the first call) against 64 separate dfr_reproject calls."""
+    target, bilinear, split precision, value and footprint; dfr_reproject_batch (a CUDA graph of
+    single-frame kernels or one kernel over the frame table, tuned on the first call) against 64
+    separate dfr_reproject calls."""
     c = synth.config2()
     tgt = dfr.to_c(c["tgt"])
     srcs = [dfr.to_c(dfr.fit_inverse_sip(sw, 4)[0]) for sw in c["src"]]
@@ -752,9 +753,10 @@ def run_oracle(args):
 
 def run_extra(args):
     """Secondary measurements (not the bench line): the batch configuration (64 uneven frames
-    onto 8192^2, one persistent graph launch vs 64 separate launches), the gradient configuration
-    (2048^2, forward + adjoint) and the stack configuration (32 x 6000x4000 -> 12000x8000,
-    batched forward + per-frame adjoint). One JSON line each."""
+    onto 8192^2, one batch call vs 64 separate launches), the gradient configuration (2048^2,
+    forward + adjoint), the stack configuration (32 x 6000x4000 -> 12000x8000, batched forward
+    + batched adjoint), every configuration in both precisions, and single-frame variants. One
+    JSON line each."""
     import torch
     import paper_2505_03932_gb300 as dfr
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

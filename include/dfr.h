@@ -157,10 +157,14 @@ int dfr_reproject_host(const dfr_wcs* src, const dfr_wcs* tgt, const float* host
  * stacks >1000 exposures, Sec. 2). Every frame's pixels are computed with exactly the
  * arithmetic of dfr_reproject for the same bounding box and flags, so results are equal bit
  * for bit. Frames with w or h == 0 are skipped. The graph is either the single-frame kernels
- * in parallel chains or one persistent kernel over a frame table (library-owned pinned and
- * device memory); a built-in autotuner picks the form on the first call per (order, flags,
- * SIP degree, log2 n) by timing the candidates on the caller's data (DFR_AUTOTUNE=0: one
- * chain, no timing). Graphs are cached and updated in place when only pointers change. */
+ * in parallel chains or one kernel over a frame table (library-owned pinned and device
+ * memory; split precision: one CTA per anchor cell of every frame, all-FP64: a persistent
+ * grid); a built-in autotuner picks the form, the chains or CTAs per SM, source-box staging
+ * on or off and, for split precision, the tile height (8, 16 or 32 target rows per staged
+ * source box) on the first call per (order, flags, SIP degree, log2 n), by timing the
+ * candidates on the caller's data (DFR_AUTOTUNE=0: one chain, tile height 16, no timing;
+ * DFR_BATCH_FORM=graph|table and DFR_TILE_H=8|16|32 restrict the search). Graphs are cached
+ * and updated in place when only pointers change. */
 int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
                         int32_t order, uint32_t flags, void* stream);
 
@@ -185,8 +189,8 @@ int dfr_reproject_batch_noalloc(const dfr_frame* frames, int32_t n, const dfr_wc
  * has no counterpart). out[5], host memory: [0] the tile height (rows of target pixels per
  * staged source box, 8, 16 or 32; 0: no staging) of the last split-precision dfr_reproject;
  * [1..4] of the last dfr_reproject_batch: form (1: a CUDA graph of single-frame kernels in
- * parallel chains, 0: one persistent kernel), chains or CTAs per SM, TMA staging (0/1), tile
- * height. Process-wide (the last call on any device or thread). DFR_ERR_INVALID_ARG if out is
+ * parallel chains, 0: one kernel over the frame table), chains or CTAs per SM, box staging
+ * (0/1), tile height. Process-wide (the last call on any device or thread). DFR_ERR_INVALID_ARG if out is
  * NULL. */
 int dfr_last_launch_config(int32_t* out);
 

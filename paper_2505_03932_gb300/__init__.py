@@ -204,7 +204,7 @@ def last_launch_config():
     v = (ctypes.c_int32 * 5)()
     _check(lib().dfr_last_launch_config(v))
     return {"single_tile_h": int(v[0]),
-            "batch": {"form": "graph" if v[1] == 1 else "persistent", "k": int(v[2]),
+            "batch": {"form": "graph" if v[1] == 1 else "table", "k": int(v[2]),
                       "tma": bool(v[3]), "tile_h": int(v[4])}}
 
 
@@ -349,7 +349,8 @@ def reproject(src_img, src_wcs, tgt_wcs, shape_out=None, bbox=None, order="bilin
 def reproject_batch(images, src_wcs_list, tgt_wcs, bboxes=None, order="bilinear",
                     precision="split", outs=None, fps=None, footprint=True, stream=None,
                     nan_mask=False, prefiltered=False, tma=True):
-    """Reproject many exposures in one persistent launch (dfr_reproject_batch).
+    """Reproject many exposures in one launch (dfr_reproject_batch: a graph of single-frame
+    kernels or one kernel over the frame table, as the autotuner picks).
 
     bboxes default to dfr_target_bbox per frame. Returns (values, footprints) lists."""
     torch = _torch()

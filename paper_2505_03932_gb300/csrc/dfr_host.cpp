@@ -567,7 +567,8 @@ struct DeviceCtx {
   bool pending = false;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   // batch configuration per (order, flags, degree, log2 n): (1, lanes, -, th) = graph of
-  // single-frame kernels in `lanes` parallel chains, (0, ctas/SM, tma, th) = persistent kernel;
+  // single-frame kernels in `lanes` parallel chains, (0, ctas/SM, tma, th) = one kernel over the
+  // frame table (split: one CTA per cell, ctas/SM unused; FP64: a persistent grid);
   // th = tile height of the split kernels
   std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int, int>> tuned;
   // fan-out graphs, keyed by the (kernel, grid, smem) signature of their frames
@@ -783,6 +784,18 @@ cudaError_t launch_single(const FwdPlan& P, cudaStream_t s) {
   return launch_forward(Pk, L, grid, forward_threads_default(), smem_for(P), s);
 }
 
+// DFR_TILE_H=8|16|32 pins the tile height of single-frame and batch launches (profiling one
+// configuration under a profiler, whose serialised launches would mislead the tuners; testing
+// every height); 0 when unset.
+int tile_height_pin() {
+  static const int pinned = [] {
+    const char* e = std::getenv("DFR_TILE_H");
+    const int v = e ? std::atoi(e) : 0;
+    return (v == 8 || v == 16 || v == 32) ? v : 0;
+  }();
+  return pinned;
+}
+
 // Launch configurations last used (dfr_last_launch_config): single-frame tile height; batch
 // form, chains or CTAs per SM, TMA, tile height.
 std::atomic<int> g_last_cfg[5];
@@ -805,13 +818,7 @@ int single_tile_height(const dfr_wcs* src, const dfr_wcs* tgt, const float* img,
                        int32_t y0, int32_t w, int32_t h, int32_t order, uint32_t flags,
                        cudaStream_t s) {
   if (!src || !tgt || w <= 0 || h <= 0) return kDefaultTileH;
-  // DFR_TILE_H=8|16|32 pins the height (profiling one configuration under a profiler, whose
-  // serialised launches would mislead the tuner)
-  static const int pinned = [] {
-    const char* e = std::getenv("DFR_TILE_H");
-    const int v = e ? std::atoi(e) : 0;
-    return (v == 8 || v == 16 || v == 32) ? v : 0;
-  }();
+  const int pinned = tile_height_pin();
   if (pinned) return pinned;
   const int64_t px = int64_t(w) * h;
   int dev = 0;
@@ -1400,10 +1407,10 @@ int launch_fan(DeviceCtx& c, int n, int lanes, cudaStream_t s) {
 
 // Batch autotuner, timed on the caller's data (outputs are rewritten identically by every
 // candidate): for each tile height of the split kernels (8, 16, 32 rows per staged box), graphs
-// of single-frame kernels in 1, 2, 4 or up to 64 parallel chains, and the persistent kernel
-// with several CTAs per SM, with and without TMA staging. Returns the configuration tuple kept
-// in DeviceCtx::tuned: (graph of chains 1 / persistent 0, chains or CTAs per SM, TMA, tile
-// height).
+// of single-frame kernels in 1, 2, 4 or up to 64 parallel chains, and the kernel over the frame
+// table (FP64: persistent, at several CTAs per SM), with and without box staging. Returns the
+// configuration tuple kept in DeviceCtx::tuned: (graph of chains 1 / table 0, chains or CTAs
+// per SM, staging, tile height).
 std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStream_t s) {
   const int threads = forward_threads_default();
   // DFR_BATCH_FORM=graph or =table limits the search to one launch form
@@ -1416,9 +1423,12 @@ std::tuple<int, int, int, int> autotune(DeviceCtx& c, int n, int total, cudaStre
   std::vector<FwdPlan> saved(c.h_plans, c.h_plans + n);
   const bool split = (saved[0].flags & DFR_SPLIT) != 0;
   float best = 1e30f;
-  std::tuple<int, int, int, int> pick = std::make_tuple(1, 1, 1, kDefaultTileH);
+  const int th_pin = tile_height_pin();
+  std::tuple<int, int, int, int> pick =
+      std::make_tuple(1, 1, 1, (split && th_pin) ? th_pin : int(kDefaultTileH));
   for (int th : {8, 16, 32}) {
     if (!split && th != kDefaultTileH) continue;
+    if (split && th_pin && th != th_pin) continue;
     int floats = 0;
     for (int f = 0; f < n; ++f) {
       c.h_plans[f] = saved[f];
@@ -1503,8 +1513,8 @@ extern "C" int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr
   const auto tkey = std::make_tuple(order, int(flags), ideg, 31 - __builtin_clz(unsigned(n)));
   auto it = c.tuned.find(tkey);
   const bool tuned = it != c.tuned.end();
-  std::tuple<int, int, int, int> cfg =
-      tuned ? it->second : std::make_tuple(1, 1, 1, int(kDefaultTileH));
+  const int th0 = ((flags & DFR_SPLIT) && tile_height_pin()) ? tile_height_pin() : kDefaultTileH;
+  std::tuple<int, int, int, int> cfg = tuned ? it->second : std::make_tuple(1, 1, 1, th0);
   int64_t total = 0;
   for (int f = 0; f < n; ++f) {
     const dfr_frame& fr = frames[f];

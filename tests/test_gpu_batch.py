@@ -1,4 +1,4 @@
-"""GPU batch path (dfr_reproject_batch): persistent launch, CUDA graph replay and autotuned tiles
+"""GPU batch path (dfr_reproject_batch): the frame-table kernel, CUDA graph replay and autotuned tiles
 give exactly the bits of per-frame dfr_reproject calls with the same bounding boxes; sampled
 oracle parity at the full 64-frame / 8192^2 batch size."""
 import numpy as np
@@ -110,3 +110,53 @@ def test_config2_full_batch_sampled():
         assert d.max() < SPLIT_PX
         del v, f, cr
     del imgs_d, vals, fps
+
+
+_CHILD = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import test_gpu_batch as T
+from gpu_util import dfr, to_dev, torch
+tma = sys.argv[2] == "1"
+srcs, imgs, tgt = T._frames()
+imgs_d = [to_dev(i) for i in imgs]
+bbs = [dfr().target_bbox(s, tgt) for s in srcs]
+bad = []
+for order in ("bilinear", "bicubic", "lanczos3"):
+    vals, fps = dfr().reproject_batch(imgs_d, srcs, tgt, bbs, order=order, tma=tma)
+    torch().cuda.synchronize()
+    cfg = dfr().last_launch_config()["batch"]
+    for k, (s, bb) in enumerate(zip(srcs, bbs)):
+        if bb[2] == 0:
+            continue
+        v, f = dfr().reproject(imgs_d[k], s, tgt, bbox=bb, order=order, tma=tma)
+        if not (np.array_equal(vals[k].cpu().numpy(), v.cpu().numpy()) and
+                np.array_equal(fps[k].cpu().numpy(), f.cpu().numpy())):
+            bad.append((order, k))
+dfr().device_status()
+print(json.dumps({"cfg": cfg, "bad": bad}))
+"""
+
+
+@pytest.mark.parametrize("form", ["graph", "table"])
+@pytest.mark.parametrize("th", [8, 16, 32])
+@pytest.mark.parametrize("tma", [True, False])
+def test_batch_every_tuned_shape_bitwise(form, th, tma):
+    """Every configuration the batch autotuner can pick (launch form, tile height of the staged
+    boxes, box staging on or off), pinned in a child process through DFR_BATCH_FORM and
+    DFR_TILE_H: the batch gives the bits of per-frame calls."""
+    import json
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, DFR_BATCH_FORM=form, DFR_TILE_H=str(th))
+    r = subprocess.run([sys.executable, "-c", _CHILD, here, "1" if tma else "0"], env=env,
+                       capture_output=True, text=True, timeout=600,
+                       cwd=os.path.dirname(here))
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["bad"] == []
+    assert out["cfg"]["tile_h"] == th
+    assert out["cfg"]["form"] == form
