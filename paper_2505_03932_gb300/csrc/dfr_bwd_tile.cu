@@ -286,6 +286,122 @@ __device__ __forceinline__ void bwd_tile_rows(const FwdPlan& P, const HP& Q, con
   }
 }
 
+// Fast rows of a tile (interior tiles of cells with valid cubics: every pixel covered, every tap
+// inside the image and inside the staged boxes, all 32 columns and kTileH rows in the box): the
+// per-pixel work of bwd_tile_rows with the same arithmetic in the same order (so the same
+// terms), without its per-pixel coverage, masking, box and fallback branches, and with the box
+// pitch kBoxW as a compile-time constant (tap offsets are immediates).
+template <int ORDER, int IDEG, int FD>
+__device__ __forceinline__ void bwd_tile_rows_fast(const FwdPlan& P, const HP& Q,
+                                                   const BwdExtra& B, const ChainConst& K,
+                                                   const Anchor& a, const ColCubic& cc, int ox,
+                                                   int oy, int r0, int lane, const float* box,
+                                                   float* gbox, const TileBox& tb,
+                                                   bool want_params, float* acc,
+                                                   const JacCubic& J) {
+  using T = Taps<ORDER>;
+  constexpr int NTERM = nterms(FD);
+  constexpr int BW = kBoxW;
+  const int gx = ox + lane;
+  const float dx0 = float(lane - kAnchorCol);
+  const float ub = float(double(a.bx) - P.crpix_s[0]), vb = float(double(a.by) - P.crpix_s[1]);
+  const float* go = B.grad_out + int64_t(oy) * B.go_pitch + gx;
+  const int kx = a.bx + T::lo - tb.bx0, ky = a.by + T::lo - tb.by0;  // box offset of the taps
+#pragma unroll 2
+  for (int r = 0; r < kTileH; ++r) {
+    const float sr = float(r0 + r) - kCellMid;
+    const float2 pos = cubic_pos(cc, sr);
+    const float x = pos.x, y = pos.y;
+    float U = 0.f, V = 0.f;
+    if (want_params) split_uv(P, Q, a, dx0, sr, U, V);
+    const float flx = floorf(x), fly = floorf(y);
+    const float tx = x - flx, ty = y - fly;
+    int cx = int(flx) + kx, cy = int(fly) + ky;  // first tap within the box
+    if (ORDER == DFR_NEAREST) {
+      cx += tx >= 0.5f;
+      cy += ty >= 0.5f;
+    }
+    float wx[T::n], wy[T::n], dwx[T::n], dwy[T::n];
+    weights<ORDER, float>(tx, wx);
+    weights<ORDER, float>(ty, wy);
+    if (want_params) {
+      dweights<ORDER, float>(tx, dwx);
+      dweights<ORDER, float>(ty, dwy);
+    }
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) {
+      sx += wx[q];
+      sy += wy[q];
+    }
+    const float F = sx * sy;
+    const float g = go[int64_t(r) * B.go_pitch];
+    const float gF = __fdividef(g, F);
+    const int b0 = cy * BW + cx;
+    if (B.grad_src) {
+#pragma unroll
+      for (int k = 0; k < T::n; ++k) {
+        const float gw = gF * wy[k];
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) atomicAdd(gbox + b0 + k * BW + q, gw * wx[q]);
+      }
+    }
+    if (!want_params) continue;
+    float row[T::n], rowd[T::n];
+    float num = 0.f, sdx = 0.f;
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) sdx += dwx[q];
+#pragma unroll
+    for (int k = 0; k < T::n; ++k) {
+      float rw = 0.f, rd = 0.f;
+#pragma unroll
+      for (int q = 0; q < T::n; ++q) {
+        const float sv = box[b0 + k * BW + q];
+        rw = fmaf(wx[q], sv, rw);
+        rd = fmaf(dwx[q], sv, rd);
+      }
+      row[k] = rw;
+      rowd[k] = rd;
+    }
+#pragma unroll
+    for (int k = 0; k < T::n; ++k) num = fmaf(wy[k], row[k], num);
+    const float val = __fdividef(num, F);
+    float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+    for (int k = 0; k < T::n; ++k) {
+      ax_ = fmaf(wy[k], fmaf(-val, sdx, rowd[k]), ax_);
+      ay_ = fmaf(dwy[k], fmaf(-val, sx, row[k]), ay_);
+    }
+    const float gxs = gF * ax_, gys = gF * ay_;
+    float lu, lv, c[6];
+    const bool jac = FD > 0 || IDEG != 0;
+    const float2 mr0 = jac ? jac_row(J.r0, sr) : make_float2(1.f, 0.f);
+    const float2 mr1 = jac ? jac_row(J.r1, sr) : make_float2(0.f, 1.f);
+    chain_terms_m(K, gxs, gys, U, V, mr0.x, mr0.y, mr1.x, mr1.y, lu, lv, c);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] += c[q];
+    if (FD > 0) {
+      const float u = ub + x, v = vb + y;
+      float up[FD + 1], vp[FD + 1];
+      up[0] = vp[0] = 1.f;
+#pragma unroll
+      for (int e = 1; e <= FD; ++e) {
+        up[e] = up[e - 1] * u;
+        vp[e] = vp[e - 1] * v;
+      }
+      int t = 0;
+#pragma unroll
+      for (int n = 1; n <= FD; ++n)
+#pragma unroll
+        for (int p = n; p >= 0; --p, ++t) {
+          const float m = up[p] * vp[n - p];
+          acc[6 + t] = fmaf(-lu, m, acc[6 + t]);
+          acc[6 + NTERM + t] = fmaf(-lv, m, acc[6 + NTERM + t]);
+        }
+    }
+  }
+}
+
 // Adds the warp's gradient box to grad_src (non-zero elements inside the image) and clears it.
 __device__ __forceinline__ void flush_gbox(const HP& Q, const BwdExtra& B,
                                            const TileBox& tb, float* gbox, int lane) {
@@ -340,6 +456,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __gr
       Q.use_tma = P.use_tma != 0 && !P.stage_sw && !dead;
       JacCubic J;
       if ((FD > 0 || IDEG != 0) && want_params) J = fit_jacobian<IDEG, FD>(P, Q, a, lane);
+      // the fast rows need every column's cubic, bowing well inside the box margin
+      const bool fast_cell = cc.valid && !Q.mask && cox + kCellW <= Q.w &&
+                             __all_sync(0xffffffffu, cubic_bow(cc, kTileH) <= 0.5f);
       float acc[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[q] = 0.f;
@@ -361,8 +480,13 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) bwd_split_kernel(const __gr
             Q.use_tma = false;
           }
         }
-        bwd_tile_rows<ORDER, IDEG, FD>(P, Q, B, K, a, cc, cox, oy, k * kTileH, lane, box, gbox,
-                                       tb, want_params, acc, J);
+        // interior tiles of valid cells, all columns and rows present, every tap in the boxes
+        if (fast_cell && tb.use_box && tb.interior && oy + kTileH <= Q.h && Q.box_w == kBoxW)
+          bwd_tile_rows_fast<ORDER, IDEG, FD>(P, Q, B, K, a, cc, cox, oy, k * kTileH, lane, box,
+                                              gbox, tb, want_params, acc, J);
+        else
+          bwd_tile_rows<ORDER, IDEG, FD>(P, Q, B, K, a, cc, cox, oy, k * kTileH, lane, box,
+                                         gbox, tb, want_params, acc, J);
         if (tb.use_box && B.grad_src) {
           __syncwarp();
           flush_gbox(Q, B, tb, gbox, lane);
