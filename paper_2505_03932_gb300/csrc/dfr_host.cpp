@@ -729,8 +729,9 @@ uint32_t fault_tx_extra() {
 // Work units of a single-frame split launch over `cells` one-cell CTAs: the cells that fill whole
 // waves of resident CTAs stay whole; the cells of the last partial wave (all of them when the
 // frame fills less than a wave) are split into k units of fewer tiles (k a power of two up to
-// the tiles per cell, the smallest that fills a wave), so that the launch does not end on a
-// thin wave of long CTAs. Returns the grid; sets split_from and split_k.
+// the tiles per cell, the smallest whose units fill half a wave: every unit repeats its cell's
+// fit, so filling the whole wave costs more fits than it saves), so that the launch does not
+// end on a thin wave of long CTAs. Returns the grid; sets split_from and split_k.
 int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_k,
                bool batch = false, int smem = -1) {
   static std::mutex mu;
@@ -759,7 +760,7 @@ int tail_split(const FwdPlan& P, int cells, int32_t& split_from, int32_t& split_
   const int nt = kCellH / std::max(1, P.th);
   if (rest == 0) return cells;
   int kk = 1;
-  while (kk < nt && rest * kk < slots) kk *= 2;
+  while (kk < nt && 2 * rest * kk < slots) kk *= 2;
   if (kk == 1) return cells;
   split_from = cells - rest;
   split_k = kk;
