@@ -525,9 +525,11 @@ __device__ __forceinline__ void make_anchor_ff(const FwdPlan& P, float X, float 
   for (int i = 0; i < 3; ++i)
     h[i] = ff_add(ff_add(ff_mul(ff_load(P.G_ff[i][0]), u), ff_mul(ff_load(P.G_ff[i][1]), v)),
                   ff_load(P.G_ff[i][2]));
+  // 1 / h2 to about 2^-47: the FMA residual of the correctly rounded FP32 reciprocal (exact
+  // for the high part), the low part's term and one Newton correction in FP32
   const float r0 = __frcp_rn(h[2].hi);
-  const FF e = ff_add(FF{1.f, 0.f}, ff_neg(ff_mul(h[2], FF{r0, 0.f})));
-  const FF r = ff_add(FF{r0, 0.f}, ff_mul(FF{r0, 0.f}, e));
+  const float e = fmaf(-h[2].lo, r0, fmaf(-h[2].hi, r0, 1.f));
+  const FF r = ff_quick_sum(r0, __fmul_rn(r0, e));
   const FF U0 = ff_mul(h[0], r), V0 = ff_mul(h[1], r);
   const float U0f = U0.hi, V0f = V0.hi;
   const float g20 = P.G_ff[2][0][0], g21 = P.G_ff[2][1][0];

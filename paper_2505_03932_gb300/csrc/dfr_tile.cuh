@@ -180,12 +180,25 @@ static __device__ __noinline__ bool cell_point_call(const FwdPlan& P, const HP& 
 }
 
 // The common plan (no target SIP, polynomial or no inverse SIP) inlined: the double-float
-// anchor and the inverse SIP by the rolled runtime-degree Horner, whose FMA sequence (and so
-// every bit) is that of the unrolled forms cell_point_call takes.
+// anchor and the inverse SIP by the unrolled Horner of the plan's packed degree at the anchor
+// itself (offset 0), with the bits of the general evaluation there.
 __device__ __forceinline__ bool cell_point(const FwdPlan& P, const HP& Q, float X, float Y,
                                            Anchor& an, float& x, float& y) {
   make_anchor(P, X, Y, an);
-  return exact_coords_t<true>(P, Q, an, 0.f, 0.f, x, y, nullptr);
+  if (Q.identity || Q.tsip || Q.newton)
+    return exact_coords_t<true>(P, Q, an, 0.f, 0.f, x, y, nullptr);
+  // at offset 0 the local homography is the anchor itself: (U, V) = (U0, V0) and the position
+  // is f0 + (AP, BP)(U0, V0), the bits split_coords_core gives there
+  float ga = 0.f, gb = 0.f;
+  switch (P.isip_deg) {
+    case 0: break;
+    case 4: horner_pair<4, float>(P.isip_f[0], P.isip_f[1], an.U0, an.V0, ga, gb); break;
+    case 6: horner_pair<6, float>(P.isip_f[0], P.isip_f[1], an.U0, an.V0, ga, gb); break;
+    default: horner_pair<9, float>(P.isip_f[0], P.isip_f[1], an.U0, an.V0, ga, gb); break;
+  }
+  x = __fadd_rn(an.f0x, ga);
+  y = __fadd_rn(an.f0y, gb);
+  return an.h2 > 0.f;
 }
 
 __device__ __forceinline__ Anchor shfl_anchor(const Anchor& a, int src) {
