@@ -60,7 +60,8 @@ extern "C" {
 
 /* flags */
 #define DFR_FP64           0u  /* all-FP64 per pixel: the printed formulas, with libm trig   */
-#define DFR_SPLIT          1u  /* sky rotation at per-cell anchors (~48 bit), FP32 per pixel */
+#define DFR_SPLIT          1u  /* the map exactly (sky rotation in ~48-bit double-float) at */
+                               /* 20 points per 32x64 cell, per-column FP32 cubics between   */
 #define DFR_EXACT_INVERSE  2u  /* source inverse = Newton solve of A/B (AP/BP as start)      */
 #define DFR_NO_TMA         4u  /* gather straight from global memory instead of TMA tiles    */
 #define DFR_NAN_MASK       8u  /* NaN source pixels are missing: no weight in value or        */
@@ -138,7 +139,7 @@ int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
                   int32_t order, uint32_t flags, double* coords_out, void* stream);
 
 /* dfr_reproject from HOST memory to HOST memory, with the copies overlapped with the work:
- * the bounding box is cut into bands of 32-pixel cell rows; each band's source rows go
+ * the bounding box is cut into bands of 64-pixel cell rows; each band's source rows go
  * host->device on one library stream (only rows no earlier band copied), its kernel runs on a
  * second stream once they are in, and its value / footprint rows go device->host on a third,
  * so both copy directions and the compute overlap. host_img: src->naxis[1] rows, stride
