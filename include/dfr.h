@@ -177,7 +177,7 @@ int dfr_reproject_batch(const dfr_frame* frames, int32_t n, const dfr_wcs* tgt,
  * library-owned device array of about 300 KB that every GPU loading the library keeps until
  * the process exits. At most 64 frames per call (more -> DFR_ERR_INVALID_ARG, nothing
  * launched). The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. The frame table is
+ * (cudaGetSymbolAddress). The frame table is
  * copied in from a static host buffer with a pageable cudaMemcpyAsync (which waits for the
  * stream's earlier work) and the work counter is cleared on every call. Every call shares the
  * one array per device: calls whose kernels overlap on the GPU (different streams, or several
