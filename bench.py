@@ -95,13 +95,22 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def _code_of(path):
+    """A source file without its comments and blank lines: a change of comments alone leaves
+    the compiled kernel, and so a recorded capture of it, valid."""
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+    return "\n".join(line for line in lines if line.strip()).encode()
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     for f in ("dfr_fwd.cu", "dfr_fwd_kernels.cuh", "dfr_tile.cuh", "dfr_device.cuh",
               "dfr_internal.h"):
-        with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        h.update(_code_of(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f)))
     return h.hexdigest()
 
 
@@ -144,8 +153,7 @@ def fp64_source_hash():
     import hashlib
     h = hashlib.sha256()
     for f in ("dfr_fwd_kernels.cuh", "dfr_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        h.update(_code_of(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc", f)))
     return h.hexdigest()
 
 

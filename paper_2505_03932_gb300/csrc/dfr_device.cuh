@@ -445,9 +445,10 @@ __device__ __forceinline__ bool source_from_target_fp64(const FwdPlan& P, double
 }
 
 // ---------------------------------------------------------------- split-precision anchor
-// Wide-precision part of the split path, once per 32x32 cell: the homography at the cell's
-// anchor pixel (double-float, or FP64 with a target SIP), the anchor's source position split
-// into integer and fractional parts, and the FP32 coefficients of the local expansion.
+// Wide-precision part of the split path, at each cell-fit node and at the cell's anchor: the
+// homography at that target position (double-float, or FP64 with a target SIP), the source
+// position split into integer and fractional parts, and the FP32 coefficients of the local
+// expansion around it.
 struct Anchor {
   int32_t bx, by;        // integer part of the anchor's source position
   float f0x, f0y;        // anchor source position minus (bx, by)

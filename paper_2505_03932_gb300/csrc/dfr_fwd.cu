@@ -5,9 +5,10 @@
 // shared memory by a 2-D TMA load (or gathered straight from global memory), the footprint
 // computed from the in-bounds weights, value and footprint stored coalesced.
 //
-// Work units: FP64 path, a 32x8 tile per CTA; split path, a 32x64 cell per one-warp CTA. A CTA takes one unit (grid launch) or loops over units taken from an
-// atomic counter (persistent batch launch); the per-pixel arithmetic depends only on the pixel
-// and its cell, so both launch forms give equal bits.
+// Work units: FP64 path, a 32x8 tile per CTA; split path, a 32x64 cell per one-warp CTA. A
+// split CTA takes one unit (one frame, or a cell of a frame table); the FP64 batch kernel loops
+// over tiles taken from an atomic counter (a persistent grid). The per-pixel arithmetic
+// depends only on the pixel and its cell, so every launch form gives equal bits.
 #include <climits>
 
 #include "dfr_fwd_kernels.cuh"

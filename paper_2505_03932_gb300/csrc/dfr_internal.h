@@ -114,7 +114,7 @@ struct FwdLaunch {
   int32_t nframes;
   int32_t total_tiles;       // single frame: work units (tiles or cells; batch reads
                              // tile_start[n])
-  int32_t* counter;          // batch: device work counter (persistent loop); nullptr: grid
+  int32_t* counter;          // FP64 batch: device work counter of the persistent grid
   int32_t box_floats;        // floats of each warp's source-box buffer, a multiple of 32
   int32_t unit_begin;        // single-frame split launch: first work unit (a band of the box)
   int32_t split_from;        // single frame: cells from this one on are split into split_k
