@@ -307,6 +307,19 @@ __device__ __forceinline__ void bwd_tile_rows_fast(const FwdPlan& P, const HP& Q
   const float ub = float(double(a.bx) - P.crpix_s[0]), vb = float(double(a.by) - P.crpix_s[1]);
   const float* go = B.grad_out + int64_t(oy) * B.go_pitch + gx;
   const int kx = a.bx + T::lo - tb.bx0, ky = a.by + T::lo - tb.by0;  // box offset of the taps
+  // The gradient taps of successive rows, summed in registers over the window of box rows
+  // they share: when the next row's taps start one box row lower in the same column, the
+  // window's first row goes to the gradient box and the window moves down one row; any other
+  // step sends the whole window. (Successive target rows of a column usually step one source
+  // row: 4 shared-memory atomics per pixel instead of 16.) With the Newton inverse's 46
+  // accumulators the window's registers would spill: there every tap goes straight to the box.
+  constexpr bool WIN = FD == 0;
+  float win[T::n][T::n];
+  int wb = -1;  // box index of the window's first tap; -1: empty
+  auto send_row = [&](int w) {
+#pragma unroll
+    for (int q = 0; q < T::n; ++q) atomicAdd(gbox + wb + w * BW + q, win[w][q]);
+  };
 #pragma unroll 2
   for (int r = 0; r < kTileH; ++r) {
     const float sr = float(r0 + r) - kCellMid;
@@ -338,13 +351,46 @@ __device__ __forceinline__ void bwd_tile_rows_fast(const FwdPlan& P, const HP& Q
     const float g = go[int64_t(r) * B.go_pitch];
     const float gF = __fdividef(g, F);
     const int b0 = cy * BW + cx;
-    if (B.grad_src) {
+    if (!WIN && B.grad_src) {
 #pragma unroll
       for (int k = 0; k < T::n; ++k) {
         const float gw = gF * wy[k];
 #pragma unroll
         for (int q = 0; q < T::n; ++q) atomicAdd(gbox + b0 + k * BW + q, gw * wx[q]);
       }
+    }
+    if (WIN && B.grad_src) {
+      float t[T::n][T::n];
+#pragma unroll
+      for (int k = 0; k < T::n; ++k) {
+        const float gw = gF * wy[k];
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) t[k][q] = gw * wx[q];
+      }
+      if (b0 == wb + BW) {  // one box row down: send the window's first row, move it down
+        send_row(0);
+#pragma unroll
+        for (int k = 0; k + 1 < T::n; ++k)
+#pragma unroll
+          for (int q = 0; q < T::n; ++q) win[k][q] = win[k + 1][q];
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) win[T::n - 1][q] = 0.f;
+        wb = b0;
+      } else if (b0 != wb) {  // elsewhere: send the whole window, start a new one
+        if (wb >= 0) {
+#pragma unroll
+          for (int k = 0; k < T::n; ++k) send_row(k);
+        }
+#pragma unroll
+        for (int k = 0; k < T::n; ++k)
+#pragma unroll
+          for (int q = 0; q < T::n; ++q) win[k][q] = 0.f;
+        wb = b0;
+      }
+#pragma unroll
+      for (int k = 0; k < T::n; ++k)
+#pragma unroll
+        for (int q = 0; q < T::n; ++q) win[k][q] += t[k][q];
     }
     if (!want_params) continue;
     float row[T::n], rowd[T::n];
@@ -399,6 +445,10 @@ __device__ __forceinline__ void bwd_tile_rows_fast(const FwdPlan& P, const HP& Q
           acc[6 + NTERM + t] = fmaf(-lv, m, acc[6 + NTERM + t]);
         }
     }
+  }
+  if (WIN && B.grad_src && wb >= 0) {
+#pragma unroll
+    for (int k = 0; k < T::n; ++k) send_row(k);
   }
 }
 
