@@ -1,7 +1,7 @@
 """GPU parity of the adjoint (dfr_reproject_backward) with the oracle, through the C ABI.
 
   * grad_src: equals the oracle's interpolation adjoint applied at the GPU's own coordinates,
-    element by element (|d| <= 1e-5 * max|grad_src|); the GPU pair (forward, backward) passes
+    element by element (|d| <= 1e-5 |g_i| + 1e-6 max|g|); the GPU pair (forward, backward) passes
     the dot-product test <W s, g> = <s, W^T g> to 1e-5.
   * grad_params: given the same output gradient, equals the oracle's forward-mode dual-number
     gradient to 1e-4 * max(|g_ref|, 1e-3 * max |g_group|) (CRVAL, CD, SIP groups).
@@ -69,6 +69,8 @@ def test_grad_src_matches_oracle_adjoint(order, precision):
                                  OR.ORDERS[order], g.ravel(), valid=ok,
                                  use_snap=(precision == "fp64"))
     assert np.abs(gs - ref).max() <= 1e-5 * np.abs(ref).max()
+    # per element: FP32 rounding of each sum (relative) plus a floor for sums that cancel
+    assert np.all(np.abs(gs - ref) <= 1e-5 * np.abs(ref) + 1e-6 * np.abs(ref).max())
     # dot-product test of the GPU pair
     s = synth.rng_for(10).standard_normal((n, n)).astype(np.float32)
     ws, _ = dfr().reproject(to_dev(s), src, tgt, bbox=bbox, order=order, precision=precision)
@@ -259,7 +261,7 @@ def test_autograd_alignment_descent():
             g = theta.grad * scale
             step = 0.05 * 0.93 ** it  # arcsec, decaying
             theta -= step * g * scale / max(float(g.abs().max()), 1e-30)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     err = (theta.detach().cpu().numpy()[:2] - np.array(truth["crval"])) * 3600
     assert losses[-1] < 0.05 * losses[0]
     assert np.all(np.abs(err) < 0.02)
