@@ -345,11 +345,12 @@ void set_tile_height(FwdPlan& P, int th) {
   const int ext = (P.order == DFR_LANCZOS3) ? 6
                   : (P.order == DFR_BICUBIC || P.order == DFR_BSPLINE3) ? 4 : 2;
   // (the Jacobian varies slowly; 3 % over its sampled maximum, and tiles whose taps still do
-  // not fit the box take the per-pixel path)
+  // not fit the box take the per-pixel path). A tile's rows span floor(y_max) - floor(y_min) +
+  // taps <= ceil(dy) + taps source rows, plus the margin on both sides.
   const double sx = 1.03 * (double(P.jac[0]) * (kCellW - 1) + double(P.jac[1]) * B) + 1.0;
-  const double sy = 1.03 * (double(P.jac[2]) * (kCellW - 1) + double(P.jac[3]) * B) + 1.0;
+  const double sy = 1.03 * (double(P.jac[2]) * (kCellW - 1) + double(P.jac[3]) * B);
   const int bw = int(std::ceil(sx)) + 1 + ext + 3 + 2 * P.box_margin;
-  const int bh = int(std::ceil(sy)) + 1 + ext + 2 * P.box_margin;
+  const int bh = int(std::ceil(sy)) + ext + 2 * P.box_margin;
   if (bw > kBoxW || bh > 256 || smem_for_floats(kBoxW * bh) > 110 * 1024) return;
   if (P.tma_ok == 2) {  // a source TMA cannot describe: asynchronous per-thread copies
     P.box_w = kBoxW;
