@@ -131,7 +131,12 @@ int dfr_target_bbox(const dfr_wcs* src, const dfr_wcs* tgt, int32_t bbox[4]);
  * | DFR_EXACT_INVERSE | DFR_NO_TMA | DFR_NAN_MASK. Without DFR_NAN_MASK, NaN source pixels
  * propagate into the values they touch. coords_out (nullable, device): 2*out_w*out_h doubles,
  * the source position (x then y per pixel, row-major) exactly as the kernel used it, NaN where
- * the projection is undefined. Asynchronous on `stream`; out/footprint are written in full. */
+ * the projection is undefined. Asynchronous on `stream`; out/footprint are written in full.
+ * Split-precision frames of at least 2^22 output pixels tune the kernel's tile height (8, 16
+ * or 32 target rows per staged source box) on their first call per (order, flags, inverse
+ * degree, size class) by timing the three on the caller's arguments (each writes the same
+ * bits; that first call synchronises the stream); DFR_AUTOTUNE=0, or a stream being
+ * captured, keeps 16, DFR_TILE_H=8|16|32 pins it. */
 int dfr_reproject(const dfr_wcs* src, const dfr_wcs* tgt,
                   const float* src_img, int64_t src_pitch,
                   float* out, float* footprint, int64_t out_pitch,
