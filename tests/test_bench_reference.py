@@ -20,3 +20,25 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["cores"] == cores
     assert line["config"]["sample_pixels_per_step"] == 250_000 * cores
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_recorded_captures_follow_the_kernel_code(tmp_path):
+    """The bench line reports a recorded ncu capture only while the kernel sources match it: a
+    change of comments keeps the record, a change of code drops it."""
+    import importlib.util
+    import shutil
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert b.recorded_traffic() is not None and b.recorded_fp64() is not None
+    csrc = tmp_path / "paper_2505_03932_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_2505_03932_gb300", "csrc"), csrc)
+    shutil.copytree(os.path.join(ROOT, "profiles"), tmp_path / "profiles")
+    b.ROOT = str(tmp_path)
+    k = csrc / "dfr_fwd_kernels.cuh"
+    text = k.read_text()
+    k.write_text("// a comment\n" + text.replace("\n", "\n/* another */\n", 1))
+    assert b.recorded_traffic() is not None and b.recorded_fp64() is not None
+    k.write_text(text.replace("constexpr int kSplitMinBlocks = 16;",
+                              "constexpr int kSplitMinBlocks = 17;"))
+    assert b.recorded_traffic() is None and b.recorded_fp64() is None
